@@ -1,0 +1,345 @@
+/*
+ * asyrk_oracle.c -- plain, sequential FP64 CPU restatement of randomized
+ * Kaczmarz (RK) as the AsyRK paper (Liu, Wright, Sridhar, arXiv:1401.4780)
+ * defines it.  TEST INFRASTRUCTURE ONLY: it is called by the tests, by the
+ * smoke check and by the benchmark's CPU-baseline leg, never by the library.
+ * It shares no source with the CUDA library; the two meet only through
+ * seeded synthetic inputs.
+ *
+ * What is computed, and where the paper defines it:
+ *   - problem: consistent A x = b, A is m x n, rows a_i^T, no zero rows
+ *     (Section 1, "Introduction", the problem statement);
+ *   - row choice: row i with probability ||a_i||^2 / ||A||_F^2 (Section 1,
+ *     the description of RK just before Eq. (2));
+ *   - projection: x <- x - gamma (a_i^T x - b_i) / ||a_i||^2 * a_i, which is
+ *     Eq. (2) with a step-length factor gamma; gamma = 1 gives Eq. (2)
+ *     exactly; the full-row update of Section 5 ("Experiments": all
+ *     coordinates of supp(a_i) are updated, and on one thread the scheme is
+ *     the usual RK);
+ *   - the sampled row sequence: i.i.d. with replacement, as in the analysis
+ *     of Section 3 (Algorithm 1).
+ *
+ * The paper does not say how the random row is drawn.  The draw used here
+ * (and, independently, in the library) is:
+ *   (u0,u1,u2,u3) = Philox4x32-10(key = (seed_lo, seed_hi),
+ *                                 counter = (j_lo, j_hi, stream, 0))
+ *   bucket = floor(u0 * m / 2^32);  i = (u1 < thr[bucket]) ? bucket
+ *                                                         : alias[bucket]
+ * with Philox4x32-10 written from Salmon, Moraes, Dror and Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3" (SC'11), and the alias table built by
+ * Vose's method on q_i = w_i m / F (w_i = ||a_i||^2, F = ||A||_F^2):
+ *   - "small" (q < 1) and "large" (q >= 1) are filled in ascending i and
+ *     used as stacks (last in, first out);
+ *   - while both are non-empty: s = top of small (popped), l = top of large;
+ *     thr[s] = min(floor(q_s 2^32), 2^32 - 1), alias[s] = l,
+ *     q_l <- (q_l + q_s) - 1; if q_l < 1, l moves from large to small;
+ *   - every entry left in either stack gets thr = 2^32 - 1, alias = itself;
+ *   - if all w_i are bit-identical, the table is skipped and i = bucket.
+ *
+ * Arithmetic is round-to-nearest FP64 in the order written, with no FMA
+ * contraction (the build passes -ffp-contract=off): w_i sums val^2 in CSR
+ * order, F sums w_i in index order, a_i^T x sums in CSR order.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define OR_OK 0
+#define OR_EINVAL (-1)
+#define OR_ENOMEM (-2)
+#define OR_NOT_CONVERGED 1
+#define OR_DIVERGED 2
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al., SC'11): a 10-round Feistel-like        */
+/* bijection of the 128-bit counter, keyed by 64 bits.                  */
+/* ------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u /* golden ratio */
+#define PHILOX_W1 0xBB67AE85u /* sqrt(3) - 1 */
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                          uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { /* the key schedule adds the Weyl constants */
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------ */
+/* Problem checks: the paper's problem has no zero rows (Section 1).   */
+/* The CSR must have row_ptr[0] = 0, non-empty rows, strictly          */
+/* ascending columns in [0, n) within a row, finite values, ||a_i|| > 0 */
+/* and finite b.                                                       */
+/* ------------------------------------------------------------------ */
+int oracle_validate(int64_t m, int64_t n, const int64_t *row_ptr,
+                    const int32_t *col, const double *val, const double *b)
+{
+    if (m <= 0 || n <= 0 || m > 0x7fffffffLL || n > 0x7fffffffLL) return OR_EINVAL;
+    if (!row_ptr || !col || !val) return OR_EINVAL;
+    if (row_ptr[0] != 0) return OR_EINVAL;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t s = row_ptr[i], e = row_ptr[i + 1];
+        if (e <= s) return OR_EINVAL; /* zero row */
+        double w = 0.0;
+        for (int64_t k = s; k < e; ++k) {
+            if (col[k] < 0 || (int64_t)col[k] >= n) return OR_EINVAL;
+            if (k > s && col[k] <= col[k - 1]) return OR_EINVAL;
+            if (!isfinite(val[k])) return OR_EINVAL;
+            w += val[k] * val[k];
+        }
+        if (!(w > 0.0) || !isfinite(w)) return OR_EINVAL;
+        if (b && !isfinite(b[i])) return OR_EINVAL;
+    }
+    return OR_OK;
+}
+
+/* w_i = ||a_i||^2 in CSR order; returns F = ||A||_F^2 summed in index order. */
+double oracle_row_weights(int64_t m, const int64_t *row_ptr, const double *val,
+                          double *w)
+{
+    double F = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += val[k] * val[k];
+        w[i] = s;
+        F += s;
+    }
+    return F;
+}
+
+/* Vose's alias table; returns 1 when all weights are bit-identical (the
+ * table is then unused and left as the identity), 0 otherwise, or
+ * OR_ENOMEM. */
+int oracle_alias_build(int64_t m, const double *w, double F, uint32_t *thr,
+                       uint32_t *alias)
+{
+    int all_equal = 1;
+    for (int64_t i = 1; i < m; ++i)
+        if (memcmp(&w[i], &w[0], sizeof(double)) != 0) { all_equal = 0; break; }
+    for (int64_t i = 0; i < m; ++i) { thr[i] = 0xffffffffu; alias[i] = (uint32_t)i; }
+    if (all_equal) return 1;
+
+    double *q = (double *)malloc((size_t)m * sizeof(double));
+    int64_t *small = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    int64_t *large = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    if (!q || !small || !large) { free(q); free(small); free(large); return OR_ENOMEM; }
+    int64_t ns = 0, nl = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        q[i] = (w[i] * (double)m) / F;
+        if (q[i] < 1.0) small[ns++] = i; else large[nl++] = i;
+    }
+    while (ns > 0 && nl > 0) {
+        int64_t s = small[--ns];
+        int64_t l = large[nl - 1];
+        double t = floor(q[s] * 4294967296.0);
+        thr[s] = (t >= 4294967295.0) ? 0xffffffffu : (uint32_t)t;
+        alias[s] = (uint32_t)l;
+        q[l] = (q[l] + q[s]) - 1.0;
+        if (q[l] < 1.0) { --nl; small[ns++] = l; }
+    }
+    /* whatever remains keeps thr = 2^32-1, alias = self */
+    free(q); free(small); free(large);
+    return 0;
+}
+
+/* One draw of the row sequence at position j. */
+int64_t oracle_draw_row(uint64_t seed, uint32_t stream, uint64_t j, int64_t m,
+                        const uint32_t *thr, const uint32_t *alias, int uniform)
+{
+    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(j >> 32), stream, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t u[4];
+    oracle_philox4x32_10(ctr, key, u);
+    uint32_t bucket = (uint32_t)(((uint64_t)u[0] * (uint64_t)m) >> 32);
+    if (uniform) return (int64_t)bucket;
+    return (u[1] < thr[bucket]) ? (int64_t)bucket : (int64_t)alias[bucket];
+}
+
+void oracle_draw_rows(uint64_t seed, uint32_t stream, uint64_t j0, int64_t count,
+                      int64_t m, const uint32_t *thr, const uint32_t *alias,
+                      int uniform, int32_t *rows)
+{
+    for (int64_t t = 0; t < count; ++t)
+        rows[t] = (int32_t)oracle_draw_row(seed, stream, j0 + (uint64_t)t, m, thr,
+                                           alias, uniform);
+}
+
+/* ------------------------------------------------------------------ */
+/* Error measures.                                                      */
+/* ------------------------------------------------------------------ */
+/* ||b - A x||_2 ; the paper's plotted measure is ||Ax - b|| (Section 5). */
+double oracle_residual_norm(int64_t m, const int64_t *row_ptr, const int32_t *col,
+                            const double *val, const double *b, const double *x,
+                            double *r_out)
+{
+    double ss = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double d = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) d += val[k] * x[col[k]];
+        double r = b[i] - d;
+        if (r_out) r_out[i] = r;
+        ss += r * r;
+    }
+    return sqrt(ss);
+}
+
+/* g = A^T (A x - b): the measure ||A^T(Ax-b)||^2 of Table 2. */
+void oracle_normal_residual(int64_t m, int64_t n, const int64_t *row_ptr,
+                            const int32_t *col, const double *val, const double *b,
+                            const double *x, double *g)
+{
+    for (int64_t t = 0; t < n; ++t) g[t] = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        double d = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) d += val[k] * x[col[k]];
+        double r = d - b[i];
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) g[col[k]] += val[k] * r;
+    }
+}
+
+static double norm2(int64_t n, const double *v)
+{
+    double s = 0.0;
+    for (int64_t t = 0; t < n; ++t) s += v[t] * v[t];
+    return sqrt(s);
+}
+
+static double err_norm(int64_t n, const double *x, const double *xs)
+{
+    double s = 0.0;
+    for (int64_t t = 0; t < n; ++t) {
+        double d = x[t] - xs[t];
+        s += d * d;
+    }
+    return sqrt(s);
+}
+
+/* ------------------------------------------------------------------ */
+/* The RK iteration, Eq. (2) with step-length gamma, full-row update,   */
+/* steps j = j0 .. j0+nsteps-1 of the row sequence.  When trace arrays  */
+/* are given, step t records the row, the residual r = a_i^T x - b_i    */
+/* before the step and, with x_true, ||x_j - x*||^2 before the step.    */
+/* w must hold ||a_i||^2 (oracle_row_weights).                          */
+/* ------------------------------------------------------------------ */
+void oracle_rk_steps(int64_t m, const int64_t *row_ptr, const int32_t *col,
+                     const double *val, const double *b, const double *w,
+                     const uint32_t *thr, const uint32_t *alias, int uniform,
+                     uint64_t seed, uint32_t stream, double gamma, uint64_t j0,
+                     int64_t nsteps, double *x, int64_t n, const double *x_true,
+                     int32_t *trace_row, double *trace_r, double *trace_err2)
+{
+    for (int64_t t = 0; t < nsteps; ++t) {
+        int64_t i = oracle_draw_row(seed, stream, j0 + (uint64_t)t, m, thr, alias, uniform);
+        double dot = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) dot += val[k] * x[col[k]];
+        double r = dot - b[i];
+        if (trace_row) trace_row[t] = (int32_t)i;
+        if (trace_r) trace_r[t] = r;
+        if (trace_err2 && x_true) {
+            double e = err_norm(n, x, x_true);
+            trace_err2[t] = e * e;
+        }
+        double s = gamma * r / w[i];
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) x[col[k]] -= s * val[k];
+    }
+}
+
+typedef struct oracle_result {
+    int64_t sweeps;      /* completed sweeps (one sweep = m steps)            */
+    int64_t steps;       /* projections applied                              */
+    double rel_err;      /* ||x - x*|| / ||x*|| at exit, or -1 without x*     */
+    double rel_res;      /* ||b - A x|| / ||b|| at exit                       */
+    int32_t status;      /* OR_OK, OR_NOT_CONVERGED, OR_DIVERGED, OR_EINVAL   */
+    int32_t pad;
+} oracle_result;
+
+/* Solve to a tolerance: check every `check_every` sweeps the relative error
+ * ||x - x*|| / ||x*|| when x_true is given, else ||b - Ax|| / ||b||; stop
+ * when it is <= tol, or after max_sweeps sweeps (NOT_CONVERGED), or when the
+ * measure is not finite or has grown by 1e30 (DIVERGED).  Steps are counted
+ * from j = j0. */
+int oracle_rk_solve(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                    const double *val, const double *b, double *x, double gamma,
+                    uint64_t seed, uint32_t stream, uint64_t j0, double tol,
+                    int64_t max_sweeps, int64_t check_every, const double *x_true,
+                    oracle_result *res)
+{
+    memset(res, 0, sizeof(*res));
+    res->rel_err = -1.0;
+    int st = oracle_validate(m, n, row_ptr, col, val, b);
+    if (st != OR_OK || !(gamma > 0.0 && gamma < 2.0) || check_every <= 0 ||
+        max_sweeps < 0) {
+        res->status = OR_EINVAL;
+        return OR_EINVAL;
+    }
+    double *w = (double *)malloc((size_t)m * sizeof(double));
+    uint32_t *thr = (uint32_t *)malloc((size_t)m * sizeof(uint32_t));
+    uint32_t *alias = (uint32_t *)malloc((size_t)m * sizeof(uint32_t));
+    if (!w || !thr || !alias) {
+        free(w); free(thr); free(alias);
+        res->status = OR_ENOMEM;
+        return OR_ENOMEM;
+    }
+    double F = oracle_row_weights(m, row_ptr, val, w);
+    int uniform = oracle_alias_build(m, w, F, thr, alias);
+    if (uniform < 0) {
+        free(w); free(thr); free(alias);
+        res->status = OR_ENOMEM;
+        return OR_ENOMEM;
+    }
+
+    double ref = x_true ? norm2(n, x_true) : norm2(m, b);
+    if (!(ref > 0.0)) ref = 1.0;
+    double meas0 = x_true ? err_norm(n, x, x_true) / ref
+                          : oracle_residual_norm(m, row_ptr, col, val, b, x, NULL) / ref;
+    double meas = meas0;
+    int status = OR_NOT_CONVERGED;
+    uint64_t j = j0;
+    int64_t sweeps = 0;
+    if (meas <= tol) status = OR_OK;
+    while (status == OR_NOT_CONVERGED && sweeps < max_sweeps) {
+        int64_t k = check_every;
+        if (k > max_sweeps - sweeps) k = max_sweeps - sweeps;
+        oracle_rk_steps(m, row_ptr, col, val, b, w, thr, alias, uniform, seed, stream,
+                        gamma, j, k * m, x, n, NULL, NULL, NULL, NULL);
+        j += (uint64_t)(k * m);
+        sweeps += k;
+        meas = x_true ? err_norm(n, x, x_true) / ref
+                      : oracle_residual_norm(m, row_ptr, col, val, b, x, NULL) / ref;
+        if (!isfinite(meas) || meas > 1e30 * (meas0 > 0.0 ? meas0 : 1.0)) {
+            status = OR_DIVERGED;
+            break;
+        }
+        if (meas <= tol) status = OR_OK;
+    }
+    res->sweeps = sweeps;
+    res->steps = (int64_t)(j - j0);
+    res->rel_err = x_true ? err_norm(n, x, x_true) / ref : -1.0;
+    {
+        double bn = norm2(m, b);
+        double rn = oracle_residual_norm(m, row_ptr, col, val, b, x, NULL);
+        res->rel_res = bn > 0.0 ? rn / bn : rn;
+    }
+    res->status = status;
+    free(w); free(thr); free(alias);
+    return status;
+}

@@ -1,0 +1,119 @@
+"""Plant plausible mistakes in a copy of the oracle and check that its pins catch them.
+
+Each case rewrites one expression of ``oracle/asyrk_oracle.c`` in a temporary
+copy, builds it, runs the oracle's Python API on that build and asserts that the
+pin named beside the mistake fails.  The real oracle is never modified.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1401_4780_gb300 import synth
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "asyrk_oracle.c")
+
+
+def _build_variant(tmp_path, old, new):
+    text = open(SRC).read()
+    assert text.count(old) == 1, old
+    path = tmp_path / "variant.c"
+    path.write_text(text.replace(old, new))
+    lib = tmp_path / "libvariant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", str(lib), str(path), "-lm"])
+    return str(lib)
+
+
+def pin_step_identity():
+    s = synth.make_system(96, 24, 6, 3, row_norms="lognormal", value_dtype="f64")
+    samp = oracle.Sampler(s.m, s.row_ptr, s.val64)
+    gamma = 0.5
+    x = np.zeros(s.n)
+    rows, r, e2 = oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, s.val64, s.b, x, gamma, 77, 0, 0,
+                                  2 * s.m, sampler=samp, x_true=s.x_true, trace=True)
+    d = x - s.x_true
+    e2_next = np.append(e2[1:], d @ d)
+    # the weights from the dense definition, not from the oracle under test
+    w = np.array([np.sum(s.val64[s.row_ptr[i]:s.row_ptr[i + 1]] ** 2) for i in rows])
+    pred = e2 - gamma * (2 - gamma) * r * r / w
+    return np.max(np.abs(e2_next - pred) / e2) <= 1e-12
+
+
+def pin_row_frequencies():
+    m = 64
+    w = np.exp(np.random.default_rng(5).standard_normal(m))
+    row_ptr = np.arange(m + 1, dtype=np.int64)
+    samp = oracle.Sampler(m, row_ptr, np.sqrt(w))
+    rows = oracle.draw_rows(0xC0FFEE, 0, 0, 400_000, samp.thr, samp.alias, samp.uniform)
+    _, p = stats.chisquare(np.bincount(rows, minlength=m), w / w.sum() * rows.size)
+    return p > 1e-3
+
+
+def pin_alias_probabilities():
+    m = 1000
+    w = np.exp(2 * np.random.default_rng(1).standard_normal(m))
+    thr, alias, uniform = oracle.alias_table(w, float(w.sum()))
+    keep = thr / 2.0**32
+    p = keep.copy()
+    np.add.at(p, alias.astype(np.int64), 1 - keep)
+    return np.max(np.abs(p / m - w / w.sum())) < 1e-6 / m
+
+
+def pin_philox_counter_words():
+    # two counters that differ only in word 1 / word 2 / the key must differ,
+    # and the known first block for key 0 (cuRAND host generator, seed 0) holds
+    out = oracle.philox4x32_10([0, 0, 0, 0], [0, 0])
+    return list(out) == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+
+
+def pin_solver_reaches_tolerance():
+    s = synth.plain_f64_system(m=512, n=128, L=8)
+    x = np.zeros(s.n)
+    res = oracle.rk_solve(s.m, s.n, s.row_ptr, s.col, s.val64, s.b, x, 1.0, 5, 1e-8, 200,
+                          x_true=s.x_true)
+    err = np.linalg.norm(x - s.x_true) / np.linalg.norm(s.x_true)
+    return res.status == oracle.OK and err <= 1e-8
+
+
+MUTATIONS = [
+    ("dropped gamma", "double s = gamma * r / w[i];", "double s = r / w[i];", pin_step_identity),
+    ("sign of b", "double r = dot - b[i];", "double r = dot + b[i];", pin_step_identity),
+    ("update sign", "x[col[k]] -= s * val[k];", "x[col[k]] += s * val[k];", pin_step_identity),
+    ("norm not squared", "double s = gamma * r / w[i];", "double s = gamma * r / sqrt(w[i]);",
+     pin_step_identity),
+    ("last nonzero skipped in dot",
+     "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) dot += val[k] * x[col[k]];",
+     "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1] - 1; ++k) dot += val[k] * x[col[k]];",
+     pin_step_identity),
+    ("alias ignored", "return (u[1] < thr[bucket]) ? (int64_t)bucket : (int64_t)alias[bucket];",
+     "return (int64_t)bucket;", pin_row_frequencies),
+    ("alias coin inverted", "return (u[1] < thr[bucket]) ? (int64_t)bucket : (int64_t)alias[bucket];",
+     "return (u[1] >= thr[bucket]) ? (int64_t)bucket : (int64_t)alias[bucket];",
+     pin_row_frequencies),
+    ("Vose residual not carried", "q[l] = (q[l] + q[s]) - 1.0;", "q[l] = q[l] - 1.0;",
+     pin_alias_probabilities),
+    ("weights not squared", "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += val[k] * val[k];",
+     "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += fabs(val[k]);",
+     pin_row_frequencies),
+    ("Philox key schedule", "k1 += PHILOX_W1;", "k1 += PHILOX_W0;", pin_philox_counter_words),
+    ("Philox word swap", "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi1 ^ c3 ^ k0;",
+     pin_philox_counter_words),
+    ("stop test on wrong measure", "if (meas <= tol) status = OR_OK;\n    }",
+     "if (meas <= 1e3 * tol) status = OR_OK;\n    }", pin_solver_reaches_tolerance),
+]
+
+
+def test_pins_hold_on_the_real_oracle():
+    for _, _, _, pin in MUTATIONS:
+        assert pin()
+
+
+@pytest.mark.parametrize("name,old,new,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new, pin):
+    lib = _build_variant(tmp_path, old, new)
+    with oracle.swapped_library(lib):
+        assert not pin(), "pin did not catch: " + name
