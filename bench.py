@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark: asynchronous randomized Kaczmarz row projections per second on one GB300.
+
+Workload (default): the large async system -- m = 2^22, n = 2^20, 32 distinct
+uniformly random columns per row, N(0,1) values, row norms lognormal(0,1) (so
+rows are drawn through the alias table), FP32 values and iterate, int32 columns,
+x* ~ N(0,1), b = A x* in FP64, gamma = 1, tolerance ||x-x*||/||x*|| <= 1e-5.
+
+A step is one solve of that system from x0 = 0 to the tolerance through the C
+ABI (asyrk_solve, ASYNC mode): projection launches of one sweep each, an FP64
+check after each.  `value` = projections of all timed steps / their device time
+(CUDA events on the launch stream; inputs resident in HBM).  The matrix stream
+(1.07 GB of columns and values) is larger than the 129 MB L2, so no flush is
+needed between steps.
+
+`e2e` runs the same solve through the public API from pinned HOST buffers:
+asyrk_create (CSR and b copied to the device, row records and alias table
+built), asyrk_solve with x0/x in host memory, asyrk_destroy, all timed.
+
+`--impl reference` times the FP64 CPU oracle (test infrastructure, one thread)
+on the same workload: each step a bounded number of projections.
+
+Multi-GPU: one independent replica per rank (a single system does not shard:
+every row updates the shared x); `value` sums the replicas' projections over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "row projections/s and time to 1e-8 rel. error vs plain FP32 kernel; p50/p99 served"
+UNIT = "row projections/s"
+# algorithmic bytes per projection of the large async workload: 32 x (4 B column
+# + 4 B value) + a 16 B row record (start, length, b_i, 1/||a_i||^2) + an 8 B
+# alias entry (threshold, alias row)
+BYTES_PER_PROJECTION = 32 * 8 + 16 + 8
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_project_large_async.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1401_4780_gb300", "csrc", f)
+                  for f in ("project.cu", "common.cuh")]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["asyrk", "reference"], default="asyrk")
+    ap.add_argument("--gamma", type=float, default=1.0)
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--scale", type=int, default=0,
+                    help="shrink m and n by 2^scale (testing only; not a bench number)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self, backend=None):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            if backend is None:
+                import torch
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def reduce(self, value, op):
+        """All-reduce a float (op: "max" or "sum")."""
+        if self.pg is None:
+            return value
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per projection launch from the committed ncu summary, or None
+    when the kernel sources changed since the capture."""
+    try:
+        kv = {}
+        with open(PROFILE_SUMMARY) as f:
+            for ln in f:
+                if ":" in ln and not ln.startswith(" "):
+                    k, v = ln.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_workload(rank, scale):
+    from paper_1401_4780_gb300 import synth
+    m, n = (1 << 22) >> scale, (1 << 20) >> scale
+    return synth.large_async_system(rep=rank, m=m, n=n)
+
+
+def workload_config(s, args):
+    return {"workload": "large async system: m=2^22, n=2^20, 32 nnz/row, N(0,1) values, "
+                        "lognormal(0,1) row norms, FP32 values and x, int32 columns"
+                        if args.scale == 0 else "reduced large async system (testing)",
+            "m": s.m, "n": s.n, "nnz_per_row": 32, "nnz": s.nnz, "gamma": args.gamma,
+            "tol": args.tol, "x0": "zeros", "step": "one solve to tol from x0",
+            "l2_flush": "none: 1.07 GB column/value stream > 129 MB L2 per sweep",
+            "parallelism": "replicas (one independent system per GPU)"}
+
+
+def cpu_oracle_sample(s, gamma, target_s, seed):
+    """Projections/s of the FP64 oracle (one thread) on a bounded sample of the workload."""
+    import oracle
+    from paper_1401_4780_gb300 import synth  # noqa: F401
+    val64 = s.val64
+    samp = oracle.Sampler(s.m, s.row_ptr, val64)
+    x = np.zeros(s.n)
+    t0 = time.perf_counter()
+    calib = 200_000
+    oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, val64, s.b, x, gamma, seed, 0, 0, calib,
+                    sampler=samp)
+    dt = time.perf_counter() - t0
+    rate = calib / dt
+    nsteps = int(max(calib, min(rate * target_s, 50 * s.m)))
+    t0 = time.perf_counter()
+    oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, val64, s.b, x, gamma, seed, 0, calib, nsteps,
+                    sampler=samp)
+    dt = time.perf_counter() - t0
+    return nsteps / dt, nsteps, dt
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    from paper_1401_4780_gb300 import synth
+    s = make_workload(0, args.scale)
+    seed = synth.solver_seed(s.seed)
+    import oracle
+    val64 = s.val64
+    samp = oracle.Sampler(s.m, s.row_ptr, val64)
+    x = np.zeros(s.n)
+    # size each step to about 5 s of single-thread oracle work
+    t0 = time.perf_counter()
+    oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, val64, s.b, x, args.gamma, seed, 0, 0, 100_000,
+                    sampler=samp)
+    per_step = int(max(100_000, 100_000 / (time.perf_counter() - t0) * 5.0))
+    j = 100_000
+    for _ in range(args.warmup):
+        oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, val64, s.b, x, args.gamma, seed, 0, j,
+                        per_step, sampler=samp)
+        j += per_step
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, val64, s.b, x, args.gamma, seed, 0, j,
+                        per_step, sampler=samp)
+        times.append(time.perf_counter() - t0)
+        j += per_step
+    total = sum(times)
+    value = per_step * args.steps / total
+    sample = "%d projections per step (%.2f sweeps) of the workload, FP64 oracle, 1 thread" % (
+        per_step, per_step / s.m)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(s, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_asyrk(args, dist):
+    import torch
+
+    from paper_1401_4780_gb300 import asyrk, synth
+
+    assert torch.cuda.is_available(), "bench.py needs a GPU"
+    torch.cuda.set_device(dist.local_rank)
+    asyrk.load()
+    s = make_workload(dist.rank, args.scale)
+    seed = synth.solver_seed(s.seed)
+    stream = torch.cuda.current_stream()
+    max_sweeps = 1000
+
+    # ---------------- device-resident timed steps ----------------
+    p = asyrk.Problem.from_system(s, seed=seed)
+    x = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+    xt = torch.from_numpy(s.x_true).cuda()
+    torch.cuda.synchronize()
+
+    def step():
+        x.zero_()
+        st, info = p.solve(x, gamma=args.gamma, tol=args.tol, max_sweeps=max_sweeps, x_true=xt,
+                           device_ptrs=True, stream=stream, profile=True)
+        if st != asyrk.OK:
+            raise RuntimeError("solve status %d: %s" % (st, asyrk.asyrk_last_error()))
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local_rank)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clock = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = dist.reduce(ms, "max")
+    proj = sum(i.projections for i in infos)
+    proj_all = dist.reduce(proj, "sum")
+    launches_all = dist.reduce(sum(i.kernel_launches for i in infos), "sum")
+    value = proj_all / (ms_max / 1e3)
+
+    # dominant kernel: the projection launches, event-timed on their stream
+    proj_ms = sum(i.project_ms for i in infos)
+    proj_launches = sum(i.project_launches for i in infos)
+    per_launch_s = proj_ms / 1e3 / proj_launches
+    per_launch_proj = proj / proj_launches
+    achieved = BYTES_PER_PROJECTION * per_launch_proj / per_launch_s / 1e9
+    peak, peak_kind = read_peaks()
+    traffic = recorded_traffic()
+    sweeps = [i.sweeps for i in infos]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "kernel": "k_project<float,float,8> (one sweep per launch)",
+                "bytes_per_projection": BYTES_PER_PROJECTION,
+                "projections_per_launch": per_launch_proj,
+                "launch_ms": per_launch_s * 1e3,
+                "kernel_share_of_step": proj_ms / ms,
+                "l2_red_f32_per_s": 32 * per_launch_proj / per_launch_s,
+                "l2_gathers_per_s": 32 * per_launch_proj / per_launch_s}
+    p.close()
+
+    # ---------------- end to end from host buffers ----------------
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_rp, h_col, h_val, h_b, h_xt = (pin(s.row_ptr), pin(s.col), pin(s.val_store), pin(s.b),
+                                     pin(s.x_true))
+    h_x = torch.zeros(s.n, dtype=torch.float64).pin_memory()
+    e2e_t, e2e_proj = 0.0, 0
+    for k in range(args.e2e_steps + 1):  # the first round is a warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with asyrk.Problem(s.m, s.n, h_rp, h_col, h_val, asyrk.F32, h_b, seed=seed) as q:
+            h_x.zero_()
+            st, info = q.solve(h_x, gamma=args.gamma, tol=args.tol, max_sweeps=max_sweeps,
+                               x_true=h_xt)
+        dt = time.perf_counter() - t0
+        if st != asyrk.OK:
+            raise RuntimeError("e2e solve status %d" % st)
+        if k > 0:
+            e2e_t += dt
+            e2e_proj += info.projections
+    e2e_t = dist.reduce(e2e_t, "max")
+    e2e_proj = dist.reduce(e2e_proj, "sum")
+    h2d = (s.row_ptr.nbytes + s.col.nbytes + s.val_store.nbytes + s.b.nbytes + 8 * s.m
+           + 2 * 8 * s.n)  # CSR, b, alias table, x0, x*
+    d2h = 2 * 8 * s.m + 8 * s.n  # row weights and b back for the alias table, x
+    e2e = {"value": e2e_proj / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h),
+           "what": "asyrk_create from pinned host CSR + asyrk_solve (host x0 -> host x) + destroy"}
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1:
+        rate, nsteps, dt = cpu_oracle_sample(s, args.gamma, args.cpu_seconds, seed)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d projections (%.2f sweeps) of the same system from x0=0, FP64 "
+                         "oracle, single thread, %.1f s" % (nsteps, nsteps / s.m, dt)}
+
+    if dist.rank == 0:
+        cfg = workload_config(s, args)
+        cfg.update({"sweeps_per_step": sweeps, "workers": infos[0].workers,
+                    "subwarp": infos[0].subwarp, "time_to_tol_ms_median":
+                    statistics.median([1e3 * i.seconds for i in infos])})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": cfg, "clocks": clock, "e2e": e2e, "gpu_launches": int(launches_all),
+                "roofline": roofline, "cpu_baseline": cpu,
+                "kernel_source_sha256": kernel_source_hash()}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_asyrk(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * asyrk.h -- C ABI of libasyrk.so: asynchronous parallel randomized Kaczmarz
+ * (AsyRK; Liu, Wright, Sridhar, arXiv:1401.4780) on one NVIDIA GB300 GPU.
+ *
+ * The method solves a consistent sparse system A x = b (m x n, no zero rows;
+ * Section 1 of the paper).  Many workers on the GPU repeatedly draw a row i
+ * with probability ||a_i||^2 / ||A||_F^2 (Section 1, before Eq. (2)), read the
+ * entries of a shared iterate x on supp(a_i), form r = a_i^T x - b_i and
+ * apply the projection of Eq. (2) with a step-length factor gamma,
+ *     x_t <- x_t - gamma * r * A_it / ||a_i||^2   for every t in supp(a_i),
+ * to the shared x without locks (the full-row variant of Section 5; the
+ * lock-free shared-memory model of Section 3, where the age of the x a worker
+ * read is bounded by tau, Eq. (4), roughly the number of workers in flight).
+ *
+ * Conventions for every function below:
+ *   - Return value: ASYRK_OK (0) on success; a negative asyrk_status is a
+ *     hard error and leaves outputs unspecified; a positive status
+ *     (NOT_CONVERGED, DIVERGED) is a solver outcome with outputs filled in.
+ *     asyrk_last_error() gives a one-line description of the last hard error
+ *     raised on the calling thread.
+ *   - Pointers are host pointers unless the options say "device"; device
+ *     pointers must be CUDA global memory of the current device.
+ *   - The caller keeps ownership of every array it passes; the library
+ *     copies what it needs.  A handle owns its device memory until destroyed.
+ *   - All device work of a call is enqueued on the stream given in the
+ *     options (NULL: the legacy default stream); a call returns after that
+ *     stream has finished the call's work.
+ *   - Handles are not thread-safe: one thread at a time per handle.
+ *   - Row sampling is reproducible: projection number j of a problem draws
+ *     its row from Philox4x32-10 (Salmon et al., SC'11) with key = seed and
+ *     counter = (j mod 2^32, j div 2^32, stream id, 0): bucket =
+ *     floor(u0 * m / 2^32); row = bucket if u1 < thr[bucket] else
+ *     alias[bucket], where (thr, alias) is Vose's alias table of the row
+ *     weights ||a_i||^2 (unused when all weights are bit-identical).
+ */
+#ifndef ASYRK_H
+#define ASYRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASYRK_ABI_VERSION 1
+
+typedef struct asyrk_problem asyrk_problem; /* opaque; owns device copies of A, b, tables */
+
+typedef enum asyrk_dtype {
+    ASYRK_F64 = 0,  /* double values                                  */
+    ASYRK_F32 = 1,  /* float values                                   */
+    ASYRK_BF16 = 2  /* bfloat16 values given as uint16 bit patterns   */
+} asyrk_dtype;
+
+typedef enum asyrk_status {
+    ASYRK_OK = 0,
+    ASYRK_EINVAL = -1,        /* bad argument or malformed problem          */
+    ASYRK_ENOMEM = -2,        /* device or host allocation failed           */
+    ASYRK_ECUDA = -3,         /* a CUDA call failed                         */
+    ASYRK_ETIMEOUT = -4,      /* a bounded wait gave up                     */
+    ASYRK_NOT_CONVERGED = 1,  /* max_sweeps reached above the tolerance     */
+    ASYRK_DIVERGED = 2        /* the error measure became non-finite/huge   */
+} asyrk_status;
+
+typedef enum asyrk_mode {
+    /* One worker (one warp), FP64 iterate, projections applied strictly in
+     * order j = j0, j0+1, ...: the sequential RK iterate of Eq. (2), which is
+     * what the paper's scheme is on a single thread (Section 5). */
+    ASYRK_MODE_SEQUENTIAL = 0,
+    /* Many lock-free workers updating x with atomic adds (Section 3): x is
+     * FP64 for FP64 problems and FP32 otherwise. */
+    ASYRK_MODE_ASYNC = 1,
+    /* Mixed-precision iterative refinement (not in the paper): an FP64
+     * iterate x64; each outer step computes r = b - A x64 in FP64 on the GPU,
+     * solves A d = r with the ASYNC FP32 kernel and adds d to x64. */
+    ASYRK_MODE_REFINE = 2
+} asyrk_mode;
+
+typedef struct asyrk_create_opts {
+    uint64_t seed;       /* Philox key of the row sequence                       */
+    int32_t device_ptrs; /* 1: row_ptr, col_idx, values, b are device pointers  */
+    int32_t reserved;    /* must be 0                                            */
+    void *stream;        /* cudaStream_t for the set-up work; NULL = default     */
+} asyrk_create_opts;
+
+typedef struct asyrk_solve_opts {
+    int32_t mode;            /* asyrk_mode                                           */
+    int32_t device_ptrs;     /* 1: x and x_true are device pointers (double)         */
+    int32_t workers;         /* concurrent row workers; 0 = automatic (ASYNC/REFINE)  */
+    int32_t subwarp;         /* lanes per row: 0 = automatic, or 2, 4, 8, 16, 32      */
+    int64_t check_every;     /* sweeps between convergence checks; >= 1              */
+    const double *x_true;    /* optional x*; checks then use ||x-x*||/||x*||          */
+    void *stream;            /* cudaStream_t; NULL = legacy default stream           */
+    double inner_tol;        /* REFINE: inner solve's target relative decrease (0: 1e-3) */
+    int64_t inner_sweeps;    /* REFINE: inner sweeps per outer step (0: automatic)   */
+    int32_t profile;         /* 1: time each projection launch with CUDA events      */
+    int32_t reserved;        /* must be 0                                            */
+} asyrk_solve_opts;
+
+typedef struct asyrk_solve_info {
+    int32_t status;           /* same value as the return code                      */
+    int32_t workers;          /* workers used (tau is about this many updates)      */
+    int32_t subwarp;          /* lanes per row used                                 */
+    int32_t refine_steps;     /* REFINE: outer steps taken                          */
+    int64_t sweeps;           /* sweeps done (one sweep = m projections)            */
+    int64_t projections;      /* projections done                                   */
+    double seconds;           /* wall time of the call                              */
+    double rel_err;           /* ||x-x*||/||x*|| at exit, or -1 without x_true      */
+    double rel_res;           /* ||b-Ax||/||b|| at exit, FP64                       */
+    double project_ms;        /* profile=1: summed event time of projection launches */
+    int64_t project_launches; /* profile=1: number of projection launches timed      */
+    uint64_t j_end;           /* position of the row sequence after the call        */
+    int64_t kernel_launches;  /* GPU kernels this call launched (copies not counted) */
+} asyrk_solve_info;
+
+typedef struct asyrk_problem_stats {
+    int64_t m, n, nnz;        /* as created                                          */
+    int64_t nnz_padded;       /* stored entries after padding rows to 4-aligned starts */
+    int64_t max_row_len;      /* mu = max_i ||a_i||_0 (Section 1 notation)           */
+    int64_t device_bytes;     /* device memory held by the handle                    */
+    double frob2;             /* ||A||_F^2 in FP64                                   */
+    int32_t dtype;            /* asyrk_dtype of the stored values                   */
+    int32_t uniform;          /* 1: all row weights bit-identical, no alias table    */
+    uint64_t seed;            /* Philox key                                          */
+    uint64_t j_next;          /* next position of the row sequence                   */
+} asyrk_problem_stats;
+
+/* Create a problem from a CSR matrix A (m x n) and right-hand side b
+ * (Section 1: A x = b consistent, no zero rows).
+ *   row_ptr: m+1 int64, row_ptr[0] = 0, strictly increasing (no zero rows);
+ *   col_idx: nnz int32, strictly ascending within each row, in [0, n);
+ *   values : nnz entries of type vdtype (BF16 as uint16 bit patterns), finite,
+ *            every row with ||a_i|| > 0;
+ *   b      : m doubles, finite.
+ * Host arrays are read before the call returns; device arrays too.
+ * Errors: EINVAL (m, n outside [1, 2^31-1], a malformed CSR, a zero row,
+ * non-finite data, bad opts), ENOMEM, ECUDA.  On error *out is NULL. */
+int asyrk_create(asyrk_problem **out, int64_t m, int64_t n, const int64_t *row_ptr,
+                 const int32_t *col_idx, const void *values, int vdtype, const double *b,
+                 const asyrk_create_opts *opts);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void asyrk_destroy(asyrk_problem *p);
+
+/* Run the method from x (in: x0, out: the final iterate; n doubles, host or
+ * device per opts->device_ptrs) with step-length factor gamma in (0, 2)
+ * (sequential RK contracts only there: the derivation before Eq. (3) gives a
+ * decrease of gamma (2 - gamma) r^2/||a_i||^2 per step) until the check
+ * measure is <= tol or max_sweeps sweeps are done.  The check measure, taken
+ * every check_every sweeps in FP64 on the GPU, is ||x-x*||/||x*|| with
+ * x_true, else ||b - A x||/||b|| (Section 5 plots ||Ax-b||).  tol <= 0 runs
+ * exactly max_sweeps sweeps.  The row sequence continues from the problem's
+ * position (asyrk_set_position) and the position advances by the
+ * projections done.
+ * Returns OK, NOT_CONVERGED, DIVERGED, or EINVAL (gamma outside (0, 2),
+ * check_every < 1, max_sweeps < 0, mode or subwarp unknown, workers < 0),
+ * ENOMEM, ECUDA.  info may be NULL. */
+int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol, int64_t max_sweeps,
+                const asyrk_solve_opts *opts, asyrk_solve_info *info);
+
+/* ||b - A x||_2 / ||b||_2 in FP64 on the GPU (||b - A x|| when b = 0);
+ * x: n doubles, host or device (x_on_device).  Errors: EINVAL, ECUDA. */
+int asyrk_residual(asyrk_problem *p, const double *x, int x_on_device, double *rel_residual);
+
+/* The rows drawn by projections j0 .. j0+count-1 with Philox stream id
+ * `stream_id`, computed by the GPU sampler that the projection kernels use;
+ * rows_out: count int32 on the host.  Errors: EINVAL (count < 0), ECUDA. */
+int asyrk_draw_rows(asyrk_problem *p, uint64_t j0, int64_t count, uint32_t stream_id,
+                    int32_t *rows_out);
+
+/* Position of the row sequence: the j of the next projection.  Saving it
+ * with x and restoring both (asyrk_set_position) resumes a run; in
+ * SEQUENTIAL mode the resumed run is identical to the uninterrupted one. */
+int asyrk_get_position(asyrk_problem *p, uint64_t *j_next);
+int asyrk_set_position(asyrk_problem *p, uint64_t j_next);
+
+/* Sizes and statistics of a problem.  Errors: EINVAL. */
+int asyrk_problem_get_stats(asyrk_problem *p, asyrk_problem_stats *stats);
+
+/* Static description of a status code. */
+const char *asyrk_strerror(int status);
+
+/* One-line description of the last hard error on the calling thread. */
+const char *asyrk_last_error(void);
+
+/* ASYRK_ABI_VERSION of the loaded library. */
+int asyrk_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASYRK_H */

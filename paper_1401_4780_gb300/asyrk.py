@@ -1,0 +1,282 @@
+"""ctypes binding of the C ABI in ``include/asyrk.h`` (libasyrk.so).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  The functions carry the C names; ``Problem`` is a small owner object
+around a handle.  Arrays may be numpy arrays (host) or CUDA ``torch.Tensor``s
+(device; pass ``device_ptrs=True``).  Loading fails loudly when the library has
+not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libasyrk.so")
+
+F64, F32, BF16 = 0, 1, 2
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_CONVERGED, DIVERGED = 0, -1, -2, -3, -4, 1, 2
+MODE_SEQUENTIAL, MODE_ASYNC, MODE_REFINE = 0, 1, 2
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
+
+
+class AsyrkError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%d): %s" % (where, asyrk_strerror(status), status,
+                                               asyrk_last_error()))
+
+
+class CreateOpts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("device_ptrs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("device_ptrs", ctypes.c_int32),
+                ("workers", ctypes.c_int32), ("subwarp", ctypes.c_int32),
+                ("check_every", ctypes.c_int64), ("x_true", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p), ("inner_tol", ctypes.c_double),
+                ("inner_sweeps", ctypes.c_int64), ("profile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("workers", ctypes.c_int32),
+                ("subwarp", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("sweeps", ctypes.c_int64), ("projections", ctypes.c_int64),
+                ("seconds", ctypes.c_double), ("rel_err", ctypes.c_double),
+                ("rel_res", ctypes.c_double), ("project_ms", ctypes.c_double),
+                ("project_launches", ctypes.c_int64), ("j_end", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ProblemStats(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("nnz_padded", ctypes.c_int64), ("max_row_len", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("frob2", ctypes.c_double),
+                ("dtype", ctypes.c_int32), ("uniform", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("j_next", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["asyrk_create", "asyrk_destroy", "asyrk_solve", "asyrk_residual", "asyrk_draw_rows",
+           "asyrk_get_position", "asyrk_set_position", "asyrk_problem_get_stats",
+           "asyrk_strerror", "asyrk_last_error", "asyrk_abi_version"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libasyrk.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libasyrk.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, i64, u64, i32, u32, f64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
+                                  ctypes.c_int32, ctypes.c_uint32, ctypes.c_double)
+    lib.asyrk_create.argtypes = [ctypes.POINTER(P), i64, i64, P, P, P, ctypes.c_int, P,
+                                 ctypes.POINTER(CreateOpts)]
+    lib.asyrk_create.restype = ctypes.c_int
+    lib.asyrk_destroy.argtypes = [P]
+    lib.asyrk_destroy.restype = None
+    lib.asyrk_solve.argtypes = [P, P, f64, f64, i64, ctypes.POINTER(SolveOpts),
+                                ctypes.POINTER(SolveInfo)]
+    lib.asyrk_solve.restype = ctypes.c_int
+    lib.asyrk_residual.argtypes = [P, P, ctypes.c_int, ctypes.POINTER(f64)]
+    lib.asyrk_residual.restype = ctypes.c_int
+    lib.asyrk_draw_rows.argtypes = [P, u64, i64, u32, P]
+    lib.asyrk_draw_rows.restype = ctypes.c_int
+    lib.asyrk_get_position.argtypes = [P, ctypes.POINTER(u64)]
+    lib.asyrk_get_position.restype = ctypes.c_int
+    lib.asyrk_set_position.argtypes = [P, u64]
+    lib.asyrk_set_position.restype = ctypes.c_int
+    lib.asyrk_problem_get_stats.argtypes = [P, ctypes.POINTER(ProblemStats)]
+    lib.asyrk_problem_get_stats.restype = ctypes.c_int
+    lib.asyrk_strerror.argtypes = [ctypes.c_int]
+    lib.asyrk_strerror.restype = ctypes.c_char_p
+    lib.asyrk_last_error.argtypes = []
+    lib.asyrk_last_error.restype = ctypes.c_char_p
+    lib.asyrk_abi_version.argtypes = []
+    lib.asyrk_abi_version.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or a torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data_as(ctypes.c_void_p)
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    raise TypeError(type(a))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+def asyrk_strerror(status: int) -> str:
+    return load().asyrk_strerror(status).decode()
+
+
+def asyrk_last_error() -> str:
+    return load().asyrk_last_error().decode()
+
+
+def asyrk_abi_version() -> int:
+    return load().asyrk_abi_version()
+
+
+def asyrk_create(m, n, row_ptr, col_idx, values, vdtype, b, seed=0, device_ptrs=False,
+                 stream=None):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    o = CreateOpts(seed=seed, device_ptrs=1 if device_ptrs else 0, reserved=0,
+                   stream=_stream(stream))
+    st = load().asyrk_create(ctypes.byref(h), m, n, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
+                             vdtype, _ptr(b), ctypes.byref(o))
+    return st, h
+
+
+def asyrk_destroy(h):
+    load().asyrk_destroy(h)
+
+
+def asyrk_solve(h, x, gamma, tol, max_sweeps, opts: SolveOpts = None):
+    """x is updated in place; returns (status, SolveInfo)."""
+    info = SolveInfo()
+    st = load().asyrk_solve(h, _ptr(x), float(gamma), float(tol), int(max_sweeps),
+                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(info))
+    return st, info
+
+
+def asyrk_residual(h, x, x_on_device=False):
+    out = ctypes.c_double()
+    st = load().asyrk_residual(h, _ptr(x), 1 if x_on_device else 0, ctypes.byref(out))
+    return st, out.value
+
+
+def asyrk_draw_rows(h, j0, count, stream_id=0):
+    rows = np.zeros(count, dtype=np.int32)
+    st = load().asyrk_draw_rows(h, j0, count, stream_id, _ptr(rows))
+    return st, rows
+
+
+def asyrk_get_position(h):
+    j = ctypes.c_uint64()
+    st = load().asyrk_get_position(h, ctypes.byref(j))
+    return st, j.value
+
+
+def asyrk_set_position(h, j):
+    return load().asyrk_set_position(h, j)
+
+
+def asyrk_problem_get_stats(h):
+    s = ProblemStats()
+    st = load().asyrk_problem_get_stats(h, ctypes.byref(s))
+    return st, s
+
+
+# ---------------------------------------------------------------------------
+# owner object
+# ---------------------------------------------------------------------------
+def solve_opts(mode=MODE_ASYNC, workers=0, subwarp=0, check_every=1, x_true=None, stream=None,
+               inner_tol=0.0, inner_sweeps=0, profile=False, device_ptrs=False):
+    return SolveOpts(mode=mode, device_ptrs=1 if device_ptrs else 0, workers=workers,
+                     subwarp=subwarp, check_every=check_every, x_true=_ptr(x_true),
+                     stream=_stream(stream), inner_tol=inner_tol, inner_sweeps=inner_sweeps,
+                     profile=1 if profile else 0, reserved=0)
+
+
+class Problem:
+    """Owns one asyrk_problem handle."""
+
+    def __init__(self, m, n, row_ptr, col_idx, values, vdtype, b, seed=0, device_ptrs=False,
+                 stream=None):
+        if isinstance(vdtype, str):
+            vdtype = DTYPES[vdtype]
+        st, h = asyrk_create(m, n, row_ptr, col_idx, values, vdtype, b, seed=seed,
+                             device_ptrs=device_ptrs, stream=stream)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_create")
+        self.h = h
+        self.m, self.n = m, n
+
+    @classmethod
+    def from_system(cls, s, seed=None, **kw):
+        """From a ``synth.System`` (stored values as generated)."""
+        from . import synth
+        if seed is None:
+            seed = synth.solver_seed(s.seed)
+        return cls(s.m, s.n, s.row_ptr, s.col, s.val_store, DTYPES[s.value_dtype], s.b, seed=seed,
+                   **kw)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            asyrk_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, x, gamma=1.0, tol=1e-8, max_sweeps=1000, raise_on_error=True, **kw):
+        st, info = asyrk_solve(self.h, x, gamma, tol, max_sweeps, solve_opts(**kw))
+        if st < 0 and raise_on_error:
+            raise AsyrkError(st, "asyrk_solve")
+        return st, info
+
+    def residual(self, x, x_on_device=False):
+        st, r = asyrk_residual(self.h, x, x_on_device)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_residual")
+        return r
+
+    def draw_rows(self, j0, count, stream_id=0):
+        st, rows = asyrk_draw_rows(self.h, j0, count, stream_id)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_draw_rows")
+        return rows
+
+    @property
+    def position(self):
+        return asyrk_get_position(self.h)[1]
+
+    @position.setter
+    def position(self, j):
+        asyrk_set_position(self.h, j)
+
+    def stats(self):
+        return asyrk_problem_get_stats(self.h)[1].as_dict()

@@ -1,0 +1,174 @@
+// common.cuh -- internal types and device helpers of libasyrk.so.
+//
+// Device layout of a problem (all in HBM, written once by asyrk_create):
+//   rec[m]        32-byte row records: padded start, length, alias threshold,
+//                 alias row, b_i and 1/||a_i||^2 at FP32.  The alias entry of
+//                 bucket i and row i's own data share one 32-byte sector, so a
+//                 draw that keeps its bucket costs one sector read.
+//   col[nnz_pad]  int32 column indices, each row starting at a multiple of 4
+//                 entries (padding entries hold column 0 and value 0 and are
+//                 never used), so a lane loads 4 columns with one 16-byte load.
+//   val[nnz_pad]  values in the stored dtype, same padding.
+//   b64[m], w64[m]  b_i and ||a_i||^2 in FP64 (FP64 iterate paths, residuals).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "asyrk.h"
+
+#define ASYRK_MAX_RED_BLOCKS 1024
+
+struct __align__(32) RowRec {
+    long long start;  // first stored entry of the row (multiple of 4)
+    unsigned len;     // ||a_i||_0
+    unsigned thr;     // alias threshold of bucket i: keep i if u1 < thr
+    unsigned alias;   // alias row of bucket i
+    float b;          // b_i (or the refinement residual r_i) at FP32
+    float inv;        // 1 / ||a_i||^2 at FP32
+    unsigned pad;
+};
+static_assert(sizeof(RowRec) == 32, "row record must be one 32-byte sector");
+
+// bfloat16 stored as its 16-bit pattern; widening to FP32 is exact.
+struct bf16_t {
+    unsigned short bits;
+};
+
+struct asyrk_problem {
+    int64_t m = 0, n = 0, nnz = 0, nnz_pad = 0, max_len = 0;
+    int dtype = 0;
+    int uniform = 0;
+    int device = 0;
+    int sm_count = 0;
+    uint64_t seed = 0;
+    uint64_t j_next = 0;
+    double frob2 = 0.0;
+    double bnorm = 0.0;
+    int64_t dev_bytes = 0;
+    bool rec_b_is_residual = false;  // rec[i].b currently holds a refinement residual
+    int64_t launches = 0;            // kernels launched on behalf of this handle
+
+    RowRec *rec = nullptr;
+    int32_t *col = nullptr;
+    void *val = nullptr;
+    double *b64 = nullptr;
+    double *w64 = nullptr;
+
+    // solve workspace, allocated on first use
+    void *xw = nullptr;          // n x {float|double}: the shared iterate
+    double *x64 = nullptr;       // n: FP64 iterate / staging
+    double *xt64 = nullptr;      // n: x*
+    double *red_part = nullptr;  // reduction partials
+    unsigned *red_count = nullptr;
+    double *red_out = nullptr;   // 8 result slots
+    double *h_out = nullptr;     // pinned host copy of red_out
+    int32_t *rows_buf = nullptr;
+    int64_t rows_cap = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace asyrk {
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+int set_error(int status, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define ASYRK_CK(call)                                                      \
+    do {                                                                    \
+        cudaError_t e__ = (call);                                           \
+        if (e__ != cudaSuccess) return ::asyrk::cuda_fail(e__, #call, __FILE__, __LINE__); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies whose high and low halves are mixed with the other two counter
+// words and the key; the key is bumped by two Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+    const unsigned M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const unsigned W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const unsigned hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += W0;
+        k.y += W1;
+    }
+    return c;
+}
+
+__device__ __forceinline__ RowRec load_rec(const RowRec *p)
+{
+    const int4 *q = reinterpret_cast<const int4 *>(p);
+    int4 a = __ldg(q), b = __ldg(q + 1);
+    RowRec r;
+    r.start = (long long)(((unsigned long long)(unsigned)a.y << 32) | (unsigned)a.x);
+    r.len = (unsigned)a.z;
+    r.thr = (unsigned)a.w;
+    r.alias = (unsigned)b.x;
+    r.b = __int_as_float(b.y);
+    r.inv = __int_as_float(b.z);
+    r.pad = (unsigned)b.w;
+    return r;
+}
+
+// Row of projection j: Philox at counter (j_lo, j_hi, stream, 0), bucket =
+// floor(u0 m / 2^32), keep the bucket when u1 < thr, else take its alias.
+// Returns the row index and its record.
+__device__ __forceinline__ unsigned draw_row(unsigned long long j, unsigned stream, uint2 key,
+                                             unsigned m, int uniform, const RowRec *rec,
+                                             RowRec &out)
+{
+    const uint4 u = philox4x32_10(make_uint4((unsigned)j, (unsigned)(j >> 32), stream, 0u), key);
+    unsigned i = __umulhi(u.x, m);
+    out = load_rec(rec + i);
+    if (!uniform && u.y >= out.thr) {
+        i = out.alias;
+        out = load_rec(rec + i);
+    }
+    return i;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (defined in project.cu / measure.cu)
+// ---------------------------------------------------------------------------
+struct ProjectLaunch {
+    asyrk_problem *p;
+    void *x;               // float* or double*
+    bool x_f64;
+    double gamma;
+    unsigned long long j0;
+    unsigned long long count;  // projections in this launch
+    unsigned stream_id;
+    int workers;               // concurrent row groups
+    int subwarp;               // lanes per row group
+    bool sequential;           // one group, strictly ordered projections
+    bool b_from_rec;           // FP32 b from rec (else b64)
+    cudaStream_t stream;
+};
+int launch_project(const ProjectLaunch &L);  // counts into L.p->launches
+int project_max_workers(const asyrk_problem *p, bool x_f64, int subwarp, int *max_workers);
+int choose_subwarp(int64_t max_len, int64_t nnz, int64_t m);
+
+int launch_draw_rows(const asyrk_problem *p, unsigned long long j0, int64_t count,
+                     unsigned stream_id, int32_t *rows_dev, cudaStream_t s);
+
+// FP64 reductions; each leaves its result(s) in p->red_out[slot...]
+int launch_err2(asyrk_problem *p, const void *x, bool x_f64, const double *xt, int slot,
+                cudaStream_t s);
+int launch_sumsq(asyrk_problem *p, const double *v, int64_t n, int slot, cudaStream_t s);
+int launch_residual(asyrk_problem *p, const void *x, bool x_f64, bool write_rec_b, int slot,
+                    cudaStream_t s);
+int launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t n,
+                   cudaStream_t s);
+int launch_axpy_f32_to_f64(double *x64, const float *d, int64_t n, cudaStream_t s);
+int launch_restore_rec_b(asyrk_problem *p, cudaStream_t s);
+
+int ensure_workspace(asyrk_problem *p);
+
+}  // namespace asyrk

@@ -1,0 +1,345 @@
+// solve.cu -- asyrk_solve and asyrk_residual: the host side of a solve.
+//
+// A solve alternates launches of the projection kernel (check_every sweeps of
+// m projections each) with an FP64 check on the GPU, whose 8-byte result is
+// the only thing read back per check.  The modes:
+//   SEQUENTIAL  one worker, FP64 x, projections strictly in order (Eq. (2));
+//   ASYNC       W lock-free workers (Section 3), x in FP64 for FP64 values
+//               and FP32 otherwise;
+//   REFINE      x64 in FP64; per outer step r = b - A x64 in FP64, the ASYNC
+//               FP32 kernel solves A d = r for a number of inner sweeps, and
+//               x64 += d.  The inner sweep count adapts so that each outer
+//               step shrinks the residual by about inner_tol.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+
+#include "common.cuh"
+
+namespace asyrk {
+
+static double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// Cor. 2 asks 2 e lambda_max (tau + 1) / m <= 1 for near-linear speedup.  With
+// no lambda_max at hand the automatic worker count uses Section 1's estimate
+// for row-normalised Gaussian matrices, lambda_max ~ (1 + sqrt(m/n))^2.
+static long long tau_cap(const asyrk_problem *p)
+{
+    const double ratio = (double)p->m / (double)p->n;
+    const double lmax = (1.0 + sqrt(ratio)) * (1.0 + sqrt(ratio));
+    const double cap = (double)p->m / (2.0 * M_E * lmax) - 1.0;
+    return cap < 1.0 ? 1LL : (long long)cap;
+}
+
+struct SolveCtx {
+    asyrk_problem *p;
+    cudaStream_t s;
+    bool have_xt;
+    double ref;     // ||x*|| or ||b||
+    bool profile;
+    double project_ms = 0.0;
+    int64_t launches = 0;
+};
+
+// one projection launch, optionally bracketed by events on the launch stream
+static int project(SolveCtx &c, const ProjectLaunch &L)
+{
+    if (c.profile) ASYRK_CK(cudaEventRecord(c.p->ev[0], c.s));
+    int st = launch_project(L);
+    if (st != ASYRK_OK) return st;
+    if (c.profile) {
+        ASYRK_CK(cudaEventRecord(c.p->ev[1], c.s));
+        ASYRK_CK(cudaEventSynchronize(c.p->ev[1]));
+        float ms = 0.f;
+        ASYRK_CK(cudaEventElapsedTime(&ms, c.p->ev[0], c.p->ev[1]));
+        c.project_ms += ms;
+        c.launches += 1;
+    }
+    return ASYRK_OK;
+}
+
+// check measure of the iterate x (FP64 or FP32 on the device)
+static int measure(SolveCtx &c, const void *x, bool x_f64, double *out)
+{
+    asyrk_problem *p = c.p;
+    int st = c.have_xt ? launch_err2(p, x, x_f64, p->xt64, 0, c.s)
+                       : launch_residual(p, x, x_f64, false, 0, c.s);
+    if (st != ASYRK_OK) return st;
+    ASYRK_CK(cudaMemcpyAsync(p->h_out, p->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    ASYRK_CK(cudaStreamSynchronize(c.s));
+    *out = sqrt(p->h_out[0]) / c.ref;
+    return ASYRK_OK;
+}
+
+static int final_residual(SolveCtx &c, const double *x64, double *rel_res)
+{
+    asyrk_problem *p = c.p;
+    int st = launch_residual(p, x64, true, false, 0, c.s);
+    if (st != ASYRK_OK) return st;
+    ASYRK_CK(cudaMemcpyAsync(p->h_out, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    ASYRK_CK(cudaStreamSynchronize(c.s));
+    *rel_res = p->bnorm > 0.0 ? sqrt(p->h_out[0]) / p->bnorm : sqrt(p->h_out[0]);
+    return ASYRK_OK;
+}
+
+// element-wise helpers that do not know the handle: count their kernels here
+static int convert(asyrk_problem *p, const void *src, bool src_f64, void *dst, bool dst_f64,
+                   cudaStream_t s)
+{
+    int st = launch_convert(src, src_f64, dst, dst_f64, p->n, s);
+    if (st == ASYRK_OK && src_f64 != dst_f64) p->launches += 1;
+    return st;
+}
+
+static bool diverged(double meas, double meas0)
+{
+    return !isfinite(meas) || meas > 1e30 * (meas0 > 0.0 ? meas0 : 1.0);
+}
+
+static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps,
+                       const asyrk_solve_opts &o, asyrk_solve_info &info)
+{
+    asyrk_problem *p = c.p;
+    const bool seq = o.mode == ASYRK_MODE_SEQUENTIAL;
+    const bool x_f64 = seq || p->dtype == ASYRK_F64;
+    int G = o.subwarp ? o.subwarp : choose_subwarp(p->max_len, p->nnz, p->m);
+    long long W = 1;
+    if (!seq) {
+        int maxw = 0;
+        int st = project_max_workers(p, x_f64, G, &maxw);
+        if (st != ASYRK_OK) return st;
+        if (o.workers > 0) {
+            W = o.workers;
+        } else {
+            W = maxw;
+            const long long cap = tau_cap(p);
+            if (W > cap) W = cap;
+        }
+    }
+    info.workers = (int32_t)W;
+    info.subwarp = G;
+    if (!x_f64 && p->rec_b_is_residual) {
+        int st = launch_restore_rec_b(p, c.s);
+        if (st != ASYRK_OK) return st;
+    }
+    // the iterate: p->x64 holds x0 in FP64; work on p->xw in the kernel's precision
+    int st = convert(p, p->x64, true, p->xw, x_f64, c.s);
+    if (st != ASYRK_OK) return st;
+
+    double meas0 = 0.0, meas = 0.0;
+    if ((st = measure(c, p->xw, x_f64, &meas0)) != ASYRK_OK) return st;
+    meas = meas0;
+    int status = (tol > 0.0 && meas <= tol) ? ASYRK_OK : ASYRK_NOT_CONVERGED;
+    int64_t sweeps = 0;
+    const unsigned long long m = (unsigned long long)p->m;
+    while (status == ASYRK_NOT_CONVERGED && sweeps < max_sweeps) {
+        int64_t k = o.check_every;
+        if (k > max_sweeps - sweeps) k = max_sweeps - sweeps;
+        ProjectLaunch L;
+        L.p = p;
+        L.x = p->xw;
+        L.x_f64 = x_f64;
+        L.gamma = gamma;
+        L.j0 = p->j_next;
+        L.count = (unsigned long long)k * m;
+        L.stream_id = 0;
+        L.workers = (int)W;
+        L.subwarp = G;
+        L.sequential = seq;
+        L.b_from_rec = !x_f64;
+        L.stream = c.s;
+        if ((st = project(c, L)) != ASYRK_OK) return st;
+        p->j_next += L.count;
+        sweeps += k;
+        info.projections += (int64_t)L.count;
+        if ((st = measure(c, p->xw, x_f64, &meas)) != ASYRK_OK) return st;
+        if (diverged(meas, meas0)) {
+            status = ASYRK_DIVERGED;
+            break;
+        }
+        if (tol > 0.0 && meas <= tol) status = ASYRK_OK;
+    }
+    if (tol <= 0.0 && status == ASYRK_NOT_CONVERGED && sweeps == max_sweeps) status = ASYRK_OK;
+    info.sweeps = sweeps;
+    if ((st = convert(p, p->xw, x_f64, p->x64, true, c.s)) != ASYRK_OK) return st;
+    return status;
+}
+
+static int solve_refine(SolveCtx &c, double gamma, double tol, int64_t max_sweeps,
+                        const asyrk_solve_opts &o, asyrk_solve_info &info)
+{
+    asyrk_problem *p = c.p;
+    const int G = o.subwarp ? o.subwarp : choose_subwarp(p->max_len, p->nnz, p->m);
+    int maxw = 0;
+    int st = project_max_workers(p, false, G, &maxw);
+    if (st != ASYRK_OK) return st;
+    long long W = o.workers > 0 ? o.workers : maxw;
+    if (o.workers <= 0 && W > tau_cap(p)) W = tau_cap(p);
+    info.workers = (int32_t)W;
+    info.subwarp = G;
+    const double inner_tol = o.inner_tol > 0.0 ? o.inner_tol : 1e-3;
+    int64_t inner = o.inner_sweeps > 0 ? o.inner_sweeps : 8;
+    float *d = (float *)p->xw;
+    const unsigned long long m = (unsigned long long)p->m;
+
+    double meas0 = -1.0, meas = 0.0, rprev = -1.0;
+    int64_t sweeps = 0;
+    int status = ASYRK_NOT_CONVERGED;
+    for (;;) {
+        // r = b - A x64 in FP64, stored as the inner right-hand side
+        if ((st = launch_residual(p, p->x64, true, true, 0, c.s)) != ASYRK_OK) return st;
+        if (c.have_xt && (st = launch_err2(p, p->x64, true, p->xt64, 2, c.s)) != ASYRK_OK) return st;
+        ASYRK_CK(cudaMemcpyAsync(p->h_out, p->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        ASYRK_CK(cudaStreamSynchronize(c.s));
+        const double rnorm = sqrt(p->h_out[0]);
+        meas = c.have_xt ? sqrt(p->h_out[2]) / c.ref : rnorm / c.ref;
+        if (meas0 < 0.0) meas0 = meas;
+        if (diverged(meas, meas0)) { status = ASYRK_DIVERGED; break; }
+        if (tol > 0.0 && meas <= tol) { status = ASYRK_OK; break; }
+        if (sweeps >= max_sweeps) break;
+        if (o.inner_sweeps <= 0 && rprev > 0.0 && rnorm > 0.0) {
+            // adapt the inner sweep count to the contraction the last step achieved
+            const double rho = rnorm / rprev;
+            if (rho > 0.0 && rho < 1.0) {
+                double want = (double)inner * log(inner_tol) / log(rho);
+                if (want < 2.0) want = 2.0;
+                if (want > 4.0 * inner) want = 4.0 * inner;
+                inner = (int64_t)ceil(want);
+            } else {
+                inner *= 2;
+            }
+            if (inner > 1000) inner = 1000;
+        }
+        rprev = rnorm;
+        if (rnorm == 0.0) { status = ASYRK_OK; break; }
+        int64_t k = inner;
+        if (k > max_sweeps - sweeps) k = max_sweeps - sweeps;
+        ASYRK_CK(cudaMemsetAsync(d, 0, p->n * sizeof(float), c.s));
+        ProjectLaunch L;
+        L.p = p;
+        L.x = d;
+        L.x_f64 = false;
+        L.gamma = gamma;
+        L.j0 = p->j_next;
+        L.count = (unsigned long long)k * m;
+        L.stream_id = 0;
+        L.workers = (int)W;
+        L.subwarp = G;
+        L.sequential = false;
+        L.b_from_rec = true;
+        L.stream = c.s;
+        if ((st = project(c, L)) != ASYRK_OK) return st;
+        p->j_next += L.count;
+        sweeps += k;
+        info.projections += (int64_t)L.count;
+        if ((st = launch_axpy_f32_to_f64(p->x64, d, p->n, c.s)) != ASYRK_OK) return st;
+        p->launches += 1;
+        info.refine_steps += 1;
+    }
+    if (tol <= 0.0 && status == ASYRK_NOT_CONVERGED && sweeps >= max_sweeps) status = ASYRK_OK;
+    info.sweeps = sweeps;
+    if ((st = launch_restore_rec_b(p, c.s)) != ASYRK_OK) return st;
+    return status;
+}
+
+}  // namespace asyrk
+
+using namespace asyrk;
+
+extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol,
+                           int64_t max_sweeps, const asyrk_solve_opts *opts,
+                           asyrk_solve_info *info_out)
+{
+    const double t0 = now_s();
+    asyrk_solve_info info;
+    memset(&info, 0, sizeof info);
+    info.rel_err = -1.0;
+    if (info_out) *info_out = info;
+    if (!p || !x) return set_error(ASYRK_EINVAL, "NULL problem or x");
+    if (!(gamma > 0.0 && gamma < 2.0)) return set_error(ASYRK_EINVAL, "gamma must be in (0, 2)");
+    if (max_sweeps < 0) return set_error(ASYRK_EINVAL, "max_sweeps < 0");
+    asyrk_solve_opts o;
+    memset(&o, 0, sizeof o);
+    o.mode = ASYRK_MODE_ASYNC;
+    o.check_every = 1;
+    if (opts) o = *opts;
+    if (o.mode < ASYRK_MODE_SEQUENTIAL || o.mode > ASYRK_MODE_REFINE)
+        return set_error(ASYRK_EINVAL, "unknown mode %d", o.mode);
+    if (o.check_every < 1) return set_error(ASYRK_EINVAL, "check_every must be >= 1");
+    if (o.workers < 0) return set_error(ASYRK_EINVAL, "workers < 0");
+    if (o.subwarp != 0 && o.subwarp != 2 && o.subwarp != 4 && o.subwarp != 8 &&
+        o.subwarp != 16 && o.subwarp != 32)
+        return set_error(ASYRK_EINVAL, "subwarp must be 0, 2, 4, 8, 16 or 32");
+    if (o.reserved != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
+    if (o.mode == ASYRK_MODE_SEQUENTIAL && o.workers > 1)
+        return set_error(ASYRK_EINVAL, "SEQUENTIAL mode has one worker");
+
+    int st = ensure_workspace(p);
+    if (st != ASYRK_OK) return st;
+    const int64_t launches0 = p->launches;
+    SolveCtx c;
+    c.p = p;
+    c.s = (cudaStream_t)o.stream;
+    c.profile = o.profile != 0;
+    const cudaMemcpyKind in_kind = o.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ASYRK_CK(cudaMemcpyAsync(p->x64, x, p->n * sizeof(double), in_kind, c.s));
+    c.have_xt = o.x_true != nullptr;
+    if (c.have_xt) {
+        ASYRK_CK(cudaMemcpyAsync(p->xt64, o.x_true, p->n * sizeof(double), in_kind, c.s));
+        if ((st = launch_sumsq(p, p->xt64, p->n, 4, c.s)) != ASYRK_OK) return st;
+        ASYRK_CK(cudaMemcpyAsync(p->h_out + 4, p->red_out + 4, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        ASYRK_CK(cudaStreamSynchronize(c.s));
+        c.ref = sqrt(p->h_out[4]);
+    } else {
+        c.ref = p->bnorm;
+    }
+    if (!(c.ref > 0.0)) c.ref = 1.0;
+
+    int status = (o.mode == ASYRK_MODE_REFINE) ? solve_refine(c, gamma, tol, max_sweeps, o, info)
+                                               : solve_plain(c, gamma, tol, max_sweeps, o, info);
+    if (status < 0) {
+        if (info_out) { info.status = status; *info_out = info; }
+        return status;
+    }
+    // x64 now holds the final iterate in FP64
+    if (c.have_xt) {
+        if ((st = launch_err2(p, p->x64, true, p->xt64, 0, c.s)) != ASYRK_OK) return st;
+        ASYRK_CK(cudaMemcpyAsync(p->h_out, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        ASYRK_CK(cudaStreamSynchronize(c.s));
+        info.rel_err = sqrt(p->h_out[0]) / c.ref;
+    }
+    if ((st = final_residual(c, p->x64, &info.rel_res)) != ASYRK_OK) return st;
+    const cudaMemcpyKind out_kind = o.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    ASYRK_CK(cudaMemcpyAsync(x, p->x64, p->n * sizeof(double), out_kind, c.s));
+    ASYRK_CK(cudaStreamSynchronize(c.s));
+    info.status = status;
+    info.project_ms = c.project_ms;
+    info.project_launches = c.launches;
+    info.j_end = p->j_next;
+    info.kernel_launches = p->launches - launches0;
+    info.seconds = now_s() - t0;
+    if (info_out) *info_out = info;
+    return status;
+}
+
+extern "C" int asyrk_residual(asyrk_problem *p, const double *x, int x_on_device,
+                              double *rel_residual)
+{
+    if (!p || !x || !rel_residual) return set_error(ASYRK_EINVAL, "NULL argument");
+    int st = ensure_workspace(p);
+    if (st != ASYRK_OK) return st;
+    ASYRK_CK(cudaMemcpy(p->x64, x, p->n * sizeof(double),
+                        x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    SolveCtx c;
+    c.p = p;
+    c.s = 0;
+    c.have_xt = false;
+    c.ref = 1.0;
+    c.profile = false;
+    return final_residual(c, p->x64, rel_residual);
+}

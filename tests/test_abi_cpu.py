@@ -1,0 +1,84 @@
+"""The C-ABI library loads and exports every symbol include/asyrk.h declares (CPU only).
+
+No compute call is made here: only argument checks that return before any CUDA
+call, and the static status descriptions.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1401_4780_gb300 import asyrk
+from paper_1401_4780_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "asyrk.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build_library()
+    return asyrk.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\*?\s*(asyrk_\w+)\s*\(", text, re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("asyrk_create", "asyrk_solve", "asyrk_residual", "asyrk_destroy"):
+        assert required in names
+    assert sorted(asyrk.EXPORTS) == sorted(names)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_header():
+    # sizes implied by the header's field lists (natural alignment, LP64)
+    assert ctypes.sizeof(asyrk.CreateOpts) == 24
+    assert ctypes.sizeof(asyrk.SolveOpts) == 64
+    assert ctypes.sizeof(asyrk.SolveInfo) == 88
+    assert ctypes.sizeof(asyrk.ProblemStats) == 80
+
+
+def test_abi_version_and_status_strings(lib):
+    assert asyrk.asyrk_abi_version() == 1
+    assert asyrk.asyrk_strerror(asyrk.EINVAL).startswith("invalid")
+    assert asyrk.asyrk_strerror(asyrk.NOT_CONVERGED).startswith("tolerance")
+    assert asyrk.asyrk_strerror(12345) == "unknown status"
+
+
+@pytest.mark.parametrize("m,n", [(0, 4), (4, 0), (-1, 4), (2**31, 4), (4, 2**31)])
+def test_create_rejects_bad_sizes_before_touching_the_gpu(lib, m, n):
+    rp = np.array([0, 1], dtype=np.int64)
+    col = np.zeros(1, dtype=np.int32)
+    val = np.ones(1)
+    b = np.ones(1)
+    st, h = asyrk.asyrk_create(m, n, rp, col, val, asyrk.F64, b)
+    assert st == asyrk.EINVAL and not h.value
+    assert "m and n" in asyrk.asyrk_last_error()
+
+
+def test_create_rejects_null_arrays_and_bad_dtype(lib):
+    rp = np.array([0, 1], dtype=np.int64)
+    col = np.zeros(1, dtype=np.int32)
+    val = np.ones(1)
+    b = np.ones(1)
+    st, _ = asyrk.asyrk_create(1, 1, None, col, val, asyrk.F64, b)
+    assert st == asyrk.EINVAL
+    st, _ = asyrk.asyrk_create(1, 1, rp, col, val, 7, b)
+    assert st == asyrk.EINVAL
+
+
+def test_solve_rejects_null_handle(lib):
+    st, info = asyrk.asyrk_solve(None, np.zeros(1), 1.0, 1e-6, 1)
+    assert st == asyrk.EINVAL and info.status == 0
