@@ -325,7 +325,9 @@ def run_asyrk(args, dist):
     clock = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     ms_max = dist.reduce(ms, "max")
-    proj = sum(i.projections for i in infos)
+    # skipped projections (row exclusion) do no update: only applied ones count
+    proj = sum(i.projections - i.skipped for i in infos)
+    skipped = sum(i.skipped for i in infos)
     proj_all = dist.reduce(proj, "sum")
     launches_all = dist.reduce(sum(i.kernel_launches for i in infos), "sum")
     value = proj_all / (ms_max / 1e3)
@@ -358,7 +360,7 @@ def run_asyrk(args, dist):
                                      pin(s.x_true))
     h_x = torch.zeros(s.n, dtype=torch.float64).pin_memory()
     e2e_t, e2e_proj = 0.0, 0
-    for k in range(args.e2e_steps + 1):  # the first round is a warm-up
+    for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):  # first round warms up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with asyrk.Problem(s.m, s.n, h_rp, h_col, h_val, asyrk.F32, h_b, seed=seed) as q:
@@ -370,18 +372,18 @@ def run_asyrk(args, dist):
             raise RuntimeError("e2e solve status %d" % st)
         if k > 0:
             e2e_t += dt
-            e2e_proj += info.projections
+            e2e_proj += info.projections - info.skipped
     e2e_t = dist.reduce(e2e_t, "max")
     e2e_proj = dist.reduce(e2e_proj, "sum")
     h2d = (s.row_ptr.nbytes + s.col.nbytes + s.val_store.nbytes + s.b.nbytes + 8 * s.m
            + 2 * 8 * s.n)  # CSR, b, alias table, x0, x*
     d2h = 2 * 8 * s.m + 8 * s.n  # row weights and b back for the alias table, x
-    e2e = {"value": e2e_proj / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    e2e = None if args.e2e_steps <= 0 else {"value": e2e_proj / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h),
            "what": "asyrk_create from pinned host CSR + asyrk_solve (host x0 -> host x) + destroy"}
 
     cpu = None
-    if dist.rank == 0 and dist.world == 1:
+    if dist.rank == 0 and dist.world == 1 and args.cpu_seconds > 0:
         rate, nsteps, dt = cpu_oracle_sample(s, args.gamma, args.cpu_seconds, seed)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d projections (%.2f sweeps) of the same system from x0=0, FP64 "
@@ -390,6 +392,8 @@ def run_asyrk(args, dist):
     if dist.rank == 0:
         cfg = workload_config(s, args)
         cfg.update({"sweeps_per_step": sweeps, "workers": infos[0].workers,
+                    "skipped_fraction": skipped / max(1, skipped + proj),
+                    "row_exclusion": "on (a row held by another worker is skipped)",
                     "subwarp": infos[0].subwarp, "time_to_tol_ms_median":
                     statistics.median([1e3 * i.seconds for i in infos])})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,

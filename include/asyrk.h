@@ -26,6 +26,11 @@
  *     options (NULL: the legacy default stream); a call returns after that
  *     stream has finished the call's work.
  *   - Handles are not thread-safe: one thread at a time per handle.
+ *   - Row exclusion (ASYNC/REFINE, on by default): a worker claims its row
+ *     before reading x and skips the projection if another worker holds the
+ *     row, so no row is applied twice from the same stale x -- the property
+ *     the paper's implementation gets from giving each thread its own rows
+ *     (Section 5).  Skipped projections still advance the row sequence.
  *   - Row sampling is reproducible: projection number j of a problem draws
  *     its row from Philox4x32-10 (Salmon et al., SC'11) with key = seed and
  *     counter = (j mod 2^32, j div 2^32, stream id, 0): bucket =
@@ -95,7 +100,10 @@ typedef struct asyrk_solve_opts {
     double inner_tol;        /* REFINE: inner solve's target relative decrease (0: 1e-3) */
     int64_t inner_sweeps;    /* REFINE: inner sweeps per outer step (0: automatic)   */
     int32_t profile;         /* 1: time each projection launch with CUDA events      */
-    int32_t reserved;        /* must be 0                                            */
+    int32_t row_exclusion;   /* ASYNC/REFINE: 0 or 1 = a worker skips a row that another
+                                worker is applying (default); -1 = plain lock-free
+                                updates, where one row may be applied several times
+                                from the same stale x                                 */
 } asyrk_solve_opts;
 
 typedef struct asyrk_solve_info {
@@ -112,6 +120,8 @@ typedef struct asyrk_solve_info {
     int64_t project_launches; /* profile=1: number of projection launches timed      */
     uint64_t j_end;           /* position of the row sequence after the call        */
     int64_t kernel_launches;  /* GPU kernels this call launched (copies not counted) */
+    int64_t skipped;          /* projections skipped by row exclusion (counted in
+                                 `projections`)                                      */
 } asyrk_solve_info;
 
 typedef struct asyrk_problem_stats {

@@ -40,7 +40,7 @@ class SolveOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int64), ("x_true", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("inner_tol", ctypes.c_double),
                 ("inner_sweeps", ctypes.c_int64), ("profile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("row_exclusion", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -50,7 +50,7 @@ class SolveInfo(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("rel_err", ctypes.c_double),
                 ("rel_res", ctypes.c_double), ("project_ms", ctypes.c_double),
                 ("project_launches", ctypes.c_int64), ("j_end", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("skipped", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -205,11 +205,11 @@ def asyrk_problem_get_stats(h):
 # owner object
 # ---------------------------------------------------------------------------
 def solve_opts(mode=MODE_ASYNC, workers=0, subwarp=0, check_every=1, x_true=None, stream=None,
-               inner_tol=0.0, inner_sweeps=0, profile=False, device_ptrs=False):
+               inner_tol=0.0, inner_sweeps=0, profile=False, device_ptrs=False, row_exclusion=0):
     return SolveOpts(mode=mode, device_ptrs=1 if device_ptrs else 0, workers=workers,
                      subwarp=subwarp, check_every=check_every, x_true=_ptr(x_true),
                      stream=_stream(stream), inner_tol=inner_tol, inner_sweeps=inner_sweeps,
-                     profile=1 if profile else 0, reserved=0)
+                     profile=1 if profile else 0, row_exclusion=row_exclusion)
 
 
 class Problem:

@@ -63,6 +63,8 @@ struct asyrk_problem {
     unsigned *red_count = nullptr;
     double *red_out = nullptr;   // 8 result slots
     double *h_out = nullptr;     // pinned host copy of red_out
+    unsigned *busy = nullptr;              // ceil(m/32) row-claim words, zero between launches
+    unsigned long long *skipped = nullptr; // projections skipped by row exclusion
     int32_t *rows_buf = nullptr;
     int64_t rows_cap = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -148,6 +150,7 @@ struct ProjectLaunch {
     int workers;               // concurrent row groups
     int subwarp;               // lanes per row group
     bool sequential;           // one group, strictly ordered projections
+    bool exclusive;            // row exclusion (skip rows another worker holds)
     bool b_from_rec;           // FP32 b from rec (else b64)
     cudaStream_t stream;
 };

@@ -202,18 +202,28 @@ static void launch_row_setup(asyrk_problem *p, const int64_t *row_ptr_d, const i
 
 int ensure_workspace(asyrk_problem *p)
 {
-    if (p->xw) return ASYRK_OK;
+    if (p->ev[1]) return ASYRK_OK;
     int st;
-    if ((st = dev_alloc(p, (double **)&p->xw, (size_t)p->n)) != ASYRK_OK) return st;
-    if ((st = dev_alloc(p, &p->x64, (size_t)p->n)) != ASYRK_OK) return st;
-    if ((st = dev_alloc(p, &p->xt64, (size_t)p->n)) != ASYRK_OK) return st;
-    if ((st = dev_alloc(p, &p->red_part, (size_t)ASYRK_MAX_RED_BLOCKS * 4)) != ASYRK_OK) return st;
-    if ((st = dev_alloc(p, &p->red_count, 1)) != ASYRK_OK) return st;
-    if ((st = dev_alloc(p, &p->red_out, 8)) != ASYRK_OK) return st;
-    ASYRK_CK(cudaMemset(p->red_count, 0, sizeof(unsigned)));
-    ASYRK_CK(cudaMallocHost((void **)&p->h_out, 8 * sizeof(double)));
-    ASYRK_CK(cudaEventCreate(&p->ev[0]));
-    ASYRK_CK(cudaEventCreate(&p->ev[1]));
+    const size_t words = (size_t)((p->m + 31) / 32);
+    if (!p->xw && (st = dev_alloc(p, (double **)&p->xw, (size_t)p->n)) != ASYRK_OK) return st;
+    if (!p->x64 && (st = dev_alloc(p, &p->x64, (size_t)p->n)) != ASYRK_OK) return st;
+    if (!p->xt64 && (st = dev_alloc(p, &p->xt64, (size_t)p->n)) != ASYRK_OK) return st;
+    if (!p->red_part &&
+        (st = dev_alloc(p, &p->red_part, (size_t)ASYRK_MAX_RED_BLOCKS * 4)) != ASYRK_OK)
+        return st;
+    if (!p->red_count) {
+        if ((st = dev_alloc(p, &p->red_count, 1)) != ASYRK_OK) return st;
+        ASYRK_CK(cudaMemset(p->red_count, 0, sizeof(unsigned)));
+    }
+    if (!p->red_out && (st = dev_alloc(p, &p->red_out, 8)) != ASYRK_OK) return st;
+    if (!p->busy) {
+        if ((st = dev_alloc(p, &p->busy, words)) != ASYRK_OK) return st;
+        ASYRK_CK(cudaMemset(p->busy, 0, words * sizeof(unsigned)));
+    }
+    if (!p->skipped && (st = dev_alloc(p, &p->skipped, 1)) != ASYRK_OK) return st;
+    if (!p->h_out) ASYRK_CK(cudaMallocHost((void **)&p->h_out, 8 * sizeof(double)));
+    if (!p->ev[0]) ASYRK_CK(cudaEventCreate(&p->ev[0]));
+    if (!p->ev[1]) ASYRK_CK(cudaEventCreate(&p->ev[1]));
     return ASYRK_OK;
 }
 
@@ -235,6 +245,8 @@ static void free_problem(asyrk_problem *p)
     cudaFree(p->red_count);
     cudaFree(p->red_out);
     cudaFree(p->rows_buf);
+    cudaFree(p->busy);
+    cudaFree(p->skipped);
     if (p->h_out) cudaFreeHost(p->h_out);
     if (p->ev[0]) cudaEventDestroy(p->ev[0]);
     if (p->ev[1]) cudaEventDestroy(p->ev[1]);

@@ -40,6 +40,8 @@ struct ProjArgs {
     unsigned long long count;
     long long workers;
     double gamma;
+    unsigned *busy;                  // row-claim bits (row exclusion)
+    unsigned long long *skipped;     // projections skipped by row exclusion
 };
 
 // ---- streamed row loads: read once per projection, so marked evict-first --
@@ -107,7 +109,32 @@ __device__ __forceinline__ void scatter4(const XT (&v)[4], int4 c, int k, XT s, 
     if (k > 3) red_add(x + c.w, s * v[3]);
 }
 
-template <typename VT, typename XT, int G, bool SEQ>
+// Row exclusion: a worker claims its row in a bitmask (one bit per row, at
+// L2) with an acquire atomic OR before gathering x, and releases it with a
+// release AND after its updates.  A row already claimed is skipped: no row is
+// ever applied twice from the same stale x, the property the paper's
+// implementation gets from giving each thread its own rows (Section 5).  The
+// skipped projection would, in the sequential order, come right after the
+// same projection and change x only through the few updates in between
+// (projections are idempotent).
+__device__ __forceinline__ unsigned claim_row(unsigned *busy, unsigned i)
+{
+    unsigned old;
+    asm volatile("atom.acquire.gpu.global.or.b32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "l"(busy + (i >> 5)), "r"(1u << (i & 31))
+                 : "memory");
+    return !(old & (1u << (i & 31)));
+}
+
+__device__ __forceinline__ void release_row(unsigned *busy, unsigned i)
+{
+    asm volatile("red.release.gpu.global.and.b32 [%0], %1;" ::"l"(busy + (i >> 5)),
+                 "r"(~(1u << (i & 31)))
+                 : "memory");
+}
+
+template <typename VT, typename XT, int G, bool SEQ, bool EXCL>
 __global__ void __launch_bounds__(256) k_project(const ProjArgs a)
 {
     constexpr int GPW = 32 / G;  // workers per warp
@@ -123,18 +150,21 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs a)
     const VT *__restrict__ val = static_cast<const VT *>(a.val);
     XT *x = static_cast<XT *>(a.x);
     const XT gamma = (XT)a.gamma;
+    unsigned long long skipped = 0;
 
-    // t0 walks k*W + gbase, so worker gbase+sub gets projection t0 + sub
+    // t0 walks k*W + gbase, so worker gbase+sub gets projection t0 + sub.  The
+    // trip count is warp-uniform: every lane reaches every shuffle and barrier.
     for (unsigned long long t0 = (unsigned long long)gbase; t0 < a.count;
          t0 += (unsigned long long)W) {
         const unsigned long long t = t0 + sub;
-        const bool act = worker && t < a.count;
+        bool act = worker && t < a.count;
         long long start = 0;
         int len = 0;
+        unsigned i = 0;
         XT b = 0, scale = 0;
         if (act) {
             RowRec r;
-            const unsigned i = draw_row(a.j0 + t, a.stream_id, a.key, a.m, a.uniform, a.rec, r);
+            i = draw_row(a.j0 + t, a.stream_id, a.key, a.m, a.uniform, a.rec, r);
             start = r.start;
             len = (int)r.len;
             if (F64) {
@@ -147,15 +177,30 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs a)
         }
         int4 cc[CH];
         XT vv[CH][4];
-        XT acc = 0;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             const int off = (c * G + sl) * 4;
             if (off < len) {
                 cc[c] = ld_col4(a.col + start + off);
                 ld_val4(val + start + off, vv[c]);
-                acc += dot4(vv[c], cc[c], len - off, x);
             }
+        }
+        if (EXCL) {
+            unsigned got = 0;
+            if (act && sl == 0) got = claim_row(a.busy, i);
+            __syncwarp();  // orders the leader's acquire before the group's gathers
+            got = __shfl_sync(0xffffffffu, got, lane & ~(G - 1));
+            if (act && !got) {
+                act = false;
+                len = 0;
+                if (sl == 0) ++skipped;
+            }
+        }
+        XT acc = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int off = (c * G + sl) * 4;
+            if (off < len) acc += dot4(vv[c], cc[c], len - off, x);
         }
         for (int off = (CH * G + sl) * 4; off < len; off += 4 * G) {  // rows longer than 4*G*CH
             XT v4[4];
@@ -185,11 +230,16 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs a)
                 scatter4(v4, c4, len - off, s, x);
             }
         }
+        if (EXCL) {
+            __syncwarp();  // the group's updates happen before the leader's release
+            if (act && sl == 0) release_row(a.busy, i);
+        }
         if (SEQ) {
             __threadfence();
             __syncwarp();
         }
     }
+    if (EXCL && skipped) atomicAdd(a.skipped, skipped);
 }
 
 __global__ void k_draw_rows(const RowRec *__restrict__ rec, uint2 key, unsigned m, int uniform,
@@ -207,32 +257,34 @@ __global__ void k_draw_rows(const RowRec *__restrict__ rec, uint2 key, unsigned 
 // ---------------------------------------------------------------------------
 using KernelFn = void (*)(const ProjArgs);
 
-template <typename VT, typename XT, bool SEQ>
+template <typename VT, typename XT, bool SEQ, bool EXCL>
 static KernelFn pick_g(int G)
 {
     switch (G) {
-    case 2: return k_project<VT, XT, 2, SEQ>;
-    case 4: return k_project<VT, XT, 4, SEQ>;
-    case 8: return k_project<VT, XT, 8, SEQ>;
-    case 16: return k_project<VT, XT, 16, SEQ>;
-    case 32: return k_project<VT, XT, 32, SEQ>;
+    case 2: return k_project<VT, XT, 2, SEQ, EXCL>;
+    case 4: return k_project<VT, XT, 4, SEQ, EXCL>;
+    case 8: return k_project<VT, XT, 8, SEQ, EXCL>;
+    case 16: return k_project<VT, XT, 16, SEQ, EXCL>;
+    case 32: return k_project<VT, XT, 32, SEQ, EXCL>;
     default: return nullptr;
     }
 }
 
 template <typename VT>
-static KernelFn pick_x(bool x_f64, bool seq, int G)
+static KernelFn pick_x(bool x_f64, bool seq, bool excl, int G)
 {
-    if (seq) return x_f64 ? pick_g<VT, double, true>(G) : nullptr;
-    return x_f64 ? pick_g<VT, double, false>(G) : pick_g<VT, float, false>(G);
+    if (seq) return x_f64 ? pick_g<VT, double, true, false>(G) : nullptr;
+    if (excl)
+        return x_f64 ? pick_g<VT, double, false, true>(G) : pick_g<VT, float, false, true>(G);
+    return x_f64 ? pick_g<VT, double, false, false>(G) : pick_g<VT, float, false, false>(G);
 }
 
-static KernelFn pick_kernel(int dtype, bool x_f64, bool seq, int G)
+static KernelFn pick_kernel(int dtype, bool x_f64, bool seq, bool excl, int G)
 {
     switch (dtype) {
-    case ASYRK_F64: return pick_x<double>(x_f64, seq, G);
-    case ASYRK_F32: return pick_x<float>(x_f64, seq, G);
-    case ASYRK_BF16: return pick_x<bf16_t>(x_f64, seq, G);
+    case ASYRK_F64: return pick_x<double>(x_f64, seq, excl, G);
+    case ASYRK_F32: return pick_x<float>(x_f64, seq, excl, G);
+    case ASYRK_BF16: return pick_x<bf16_t>(x_f64, seq, excl, G);
     default: return nullptr;
     }
 }
@@ -249,7 +301,7 @@ int choose_subwarp(int64_t max_len, int64_t nnz, int64_t m)
 
 int project_max_workers(const asyrk_problem *p, bool x_f64, int subwarp, int *max_workers)
 {
-    KernelFn k = pick_kernel(p->dtype, x_f64, false, subwarp);
+    KernelFn k = pick_kernel(p->dtype, x_f64, false, true, subwarp);
     if (!k) return set_error(ASYRK_EINVAL, "no projection kernel for subwarp %d", subwarp);
     int per_sm = 0;
     ASYRK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0));
@@ -262,7 +314,8 @@ int launch_project(const ProjectLaunch &L)
 {
     asyrk_problem *p = L.p;
     if (L.count == 0) return ASYRK_OK;
-    KernelFn k = pick_kernel(p->dtype, L.x_f64, L.sequential, L.subwarp);
+    const bool excl = L.exclusive && !L.sequential;
+    KernelFn k = pick_kernel(p->dtype, L.x_f64, L.sequential, excl, L.subwarp);
     if (!k) return set_error(ASYRK_EINVAL, "no projection kernel for subwarp %d", L.subwarp);
     ProjArgs a;
     a.rec = p->rec;
@@ -278,6 +331,8 @@ int launch_project(const ProjectLaunch &L)
     a.j0 = L.j0;
     a.count = L.count;
     a.gamma = L.gamma;
+    a.busy = p->busy;
+    a.skipped = p->skipped;
     if (L.sequential) {
         a.workers = 1;
         k<<<1, 32, 0, L.stream>>>(a);

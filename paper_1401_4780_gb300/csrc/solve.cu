@@ -151,6 +151,7 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
         L.workers = (int)W;
         L.subwarp = G;
         L.sequential = seq;
+        L.exclusive = o.row_exclusion >= 0;
         L.b_from_rec = !x_f64;
         L.stream = c.s;
         if ((st = project(c, L)) != ASYRK_OK) return st;
@@ -231,6 +232,7 @@ static int solve_refine(SolveCtx &c, double gamma, double tol, int64_t max_sweep
         L.workers = (int)W;
         L.subwarp = G;
         L.sequential = false;
+        L.exclusive = o.row_exclusion >= 0;
         L.b_from_rec = true;
         L.stream = c.s;
         if ((st = project(c, L)) != ASYRK_OK) return st;
@@ -275,7 +277,8 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
     if (o.subwarp != 0 && o.subwarp != 2 && o.subwarp != 4 && o.subwarp != 8 &&
         o.subwarp != 16 && o.subwarp != 32)
         return set_error(ASYRK_EINVAL, "subwarp must be 0, 2, 4, 8, 16 or 32");
-    if (o.reserved != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
+    if (o.row_exclusion < -1 || o.row_exclusion > 1)
+        return set_error(ASYRK_EINVAL, "row_exclusion must be -1, 0 or 1");
     if (o.mode == ASYRK_MODE_SEQUENTIAL && o.workers > 1)
         return set_error(ASYRK_EINVAL, "SEQUENTIAL mode has one worker");
 
@@ -285,6 +288,7 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
     SolveCtx c;
     c.p = p;
     c.s = (cudaStream_t)o.stream;
+    ASYRK_CK(cudaMemsetAsync(p->skipped, 0, sizeof(unsigned long long), c.s));
     c.profile = o.profile != 0;
     const cudaMemcpyKind in_kind = o.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     ASYRK_CK(cudaMemcpyAsync(p->x64, x, p->n * sizeof(double), in_kind, c.s));
@@ -314,9 +318,16 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
         info.rel_err = sqrt(p->h_out[0]) / c.ref;
     }
     if ((st = final_residual(c, p->x64, &info.rel_res)) != ASYRK_OK) return st;
+    ASYRK_CK(cudaMemcpyAsync(p->h_out + 6, p->skipped, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c.s));
     const cudaMemcpyKind out_kind = o.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     ASYRK_CK(cudaMemcpyAsync(x, p->x64, p->n * sizeof(double), out_kind, c.s));
     ASYRK_CK(cudaStreamSynchronize(c.s));
+    {
+        unsigned long long sk;
+        memcpy(&sk, p->h_out + 6, sizeof sk);
+        info.skipped = (int64_t)sk;
+    }
     info.status = status;
     info.project_ms = c.project_ms;
     info.project_launches = c.launches;

@@ -70,8 +70,26 @@ def test_async_f32_lognormal_rows(gamma):
         st, info = p.solve(x, gamma=gamma, tol=1e-5, max_sweeps=500, x_true=s.x_true)
         assert st == asyrk.OK, (st, info.as_dict())
         assert info.sweeps <= 1.5 * med, (info.sweeps, med)
+        assert 0 < info.skipped < info.projections // 2  # heavy rows collide and are skipped
         err = np.linalg.norm(x - s.x_true) / np.linalg.norm(s.x_true)
         assert err <= 1e-5 and abs(err - info.rel_err) <= 1e-3 * err
+
+
+def test_plain_lock_free_updates_fail_on_heavy_rows_row_exclusion_fixes_it():
+    # rows with lognormal norms are drawn with probabilities up to ~5e-3, so with
+    # thousands of workers one row is in flight many times at once; applying its
+    # correction k times from the same stale x multiplies the error along a_i by
+    # (1 - k gamma): the iteration does not contract.  Row exclusion converges.
+    s = synth.make_system(1 << 17, 1 << 15, 32, 2024, row_norms="lognormal", value_dtype="f32")
+    with asyrk.Problem.from_system(s) as p:
+        x = np.zeros(s.n)
+        st, info = p.solve(x, tol=1e-5, max_sweeps=60, x_true=s.x_true, row_exclusion=-1,
+                           workers=4096)
+        assert st != asyrk.OK and info.skipped == 0
+        p.position = 0
+        x = np.zeros(s.n)
+        st, info = p.solve(x, tol=1e-5, max_sweeps=60, x_true=s.x_true, workers=4096)
+        assert st == asyrk.OK and info.skipped > 0
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f32"])

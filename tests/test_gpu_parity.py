@@ -69,6 +69,7 @@ def test_sequential_iterate_matches_oracle_plain_f64_workload():
         x = np.zeros(s.n)
         st, info = p.solve(x, tol=0.0, max_sweeps=5, mode=asyrk.MODE_SEQUENTIAL)
         assert st == asyrk.OK and info.projections == 5 * s.m and info.workers == 1
+        assert info.skipped == 0
         xo = _oracle_steps(s, seed, 5 * s.m)
         assert _rel(x, xo) <= 1e-12
         # continue to the oracle's converged sweep count: still the same iterate
