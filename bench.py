@@ -341,6 +341,15 @@ def run_asyrk(args, dist):
     peak, peak_kind = read_peaks()
     traffic = recorded_traffic()
     sweeps = [i.sweeps for i in infos]
+    # L2 denominators measured now on this GPU: random red.add.f32 and gathers
+    # on an array the size of x (the kernel does 32 of each per projection)
+    probe = {}
+    for name, kind in (("red_f32_per_s", asyrk.PROBE_RED_F32),
+                       ("gather_f32_per_s", asyrk.PROBE_GATHER_F32),
+                       ("gather_red_pairs_per_s", asyrk.PROBE_GATHER_RED)):
+        ops = 1 << 28
+        st_, pms = asyrk.asyrk_probe(kind, s.n, ops)
+        probe[name] = ops / (pms / 1e3) if st_ == asyrk.OK and pms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
@@ -350,8 +359,11 @@ def run_asyrk(args, dist):
                 "projections_per_launch": per_launch_proj,
                 "launch_ms": per_launch_s * 1e3,
                 "kernel_share_of_step": proj_ms / ms,
-                "l2_red_f32_per_s": 32 * per_launch_proj / per_launch_s,
-                "l2_gathers_per_s": 32 * per_launch_proj / per_launch_s}
+                "l2": {"achieved_gather_red_pairs_per_s": 32 * per_launch_proj / per_launch_s,
+                       "probe": probe,
+                       "frac_of_probe_pairs": (32 * per_launch_proj / per_launch_s /
+                                               probe["gather_red_pairs_per_s"])
+                       if probe.get("gather_red_pairs_per_s") else None}}
     p.close()
 
     # ---------------- end to end from host buffers ----------------

@@ -69,7 +69,8 @@ class ProblemStats(ctypes.Structure):
 
 EXPORTS = ["asyrk_create", "asyrk_destroy", "asyrk_solve", "asyrk_residual", "asyrk_draw_rows",
            "asyrk_get_position", "asyrk_set_position", "asyrk_problem_get_stats",
-           "asyrk_strerror", "asyrk_last_error", "asyrk_abi_version"]
+           "asyrk_strerror", "asyrk_last_error", "asyrk_abi_version", "asyrk_probe"]
+PROBE_RED_F32, PROBE_GATHER_F32, PROBE_GATHER_RED, PROBE_STREAM = 0, 1, 2, 3
 
 _lib = None
 
@@ -108,6 +109,8 @@ def load(path: str = LIB_PATH):
     lib.asyrk_last_error.restype = ctypes.c_char_p
     lib.asyrk_abi_version.argtypes = []
     lib.asyrk_abi_version.restype = ctypes.c_int
+    lib.asyrk_probe.argtypes = [ctypes.c_int, i64, i64, ctypes.POINTER(ctypes.c_float)]
+    lib.asyrk_probe.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -183,6 +186,13 @@ def asyrk_draw_rows(h, j0, count, stream_id=0):
     rows = np.zeros(count, dtype=np.int32)
     st = load().asyrk_draw_rows(h, j0, count, stream_id, _ptr(rows))
     return st, rows
+
+
+def asyrk_probe(kind, n, ops):
+    """Returns (status, kernel milliseconds) of one memory-operation probe."""
+    ms = ctypes.c_float()
+    st = load().asyrk_probe(kind, n, ops, ctypes.byref(ms))
+    return st, ms.value
 
 
 def asyrk_get_position(h):

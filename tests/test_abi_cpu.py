@@ -14,7 +14,8 @@ from paper_1401_4780_gb300 import asyrk
 from paper_1401_4780_gb300 import build as libbuild
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "asyrk.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -24,7 +25,7 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "\n".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\*?\s*(asyrk_\w+)\s*\(", text, re.M)
     return sorted(set(names))
@@ -66,6 +67,12 @@ def test_create_rejects_bad_sizes_before_touching_the_gpu(lib, m, n):
     st, h = asyrk.asyrk_create(m, n, rp, col, val, asyrk.F64, b)
     assert st == asyrk.EINVAL and not h.value
     assert "m and n" in asyrk.asyrk_last_error()
+
+
+def test_probe_rejects_bad_arguments_before_touching_the_gpu(lib):
+    assert asyrk.asyrk_probe(7, 100, 100)[0] == asyrk.EINVAL
+    assert asyrk.asyrk_probe(0, 0, 100)[0] == asyrk.EINVAL
+    assert asyrk.asyrk_probe(3, 100, 1000)[0] == asyrk.EINVAL
 
 
 def test_create_rejects_null_arrays_and_bad_dtype(lib):

@@ -142,7 +142,8 @@ def test_single_entry_rows_and_many_workers():
     # diagonal-like system: each row has one entry; RK solves it exactly
     m = n = 1000
     rng = np.random.default_rng(7)
-    val = rng.standard_normal(m) + np.sign(rng.standard_normal(m)) * 2.0
+    # |a_i| in [1, 2]: every row is drawn often enough (sampling is ~ a_i^2)
+    val = (1.0 + rng.random(m)) * np.sign(rng.standard_normal(m))
     xs = rng.standard_normal(n)
     with asyrk.Problem(m, n, np.arange(m + 1, dtype=np.int64), np.arange(n, dtype=np.int32), val,
                        asyrk.F64, val * xs) as p:
