@@ -355,6 +355,9 @@ def run_asyrk(args, dist):
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "kernel": "k_project<float,float,8> (one sweep per launch)",
+                "binding": "L2 request rate: ~64 random 4-byte gathers/red.adds per projection on "
+                           "the L2-resident x (ncu: lts__t_tag_requests 78% of peak, DRAM 6%); "
+                           "see l2.frac_of_probe_pairs",
                 "bytes_per_projection": BYTES_PER_PROJECTION,
                 "projections_per_launch": per_launch_proj,
                 "launch_ms": per_launch_s * 1e3,
