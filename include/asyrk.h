@@ -188,6 +188,38 @@ int asyrk_set_position(asyrk_problem *p, uint64_t j_next);
 /* Sizes and statistics of a problem.  Errors: EINVAL. */
 int asyrk_problem_get_stats(asyrk_problem *p, asyrk_problem_stats *stats);
 
+/* Largest m accepted by asyrk_residual_noalloc. */
+#define ASYRK_NOALLOC_MAX_ROWS 16777216
+
+/* ||b - A x||_2 (out[0]) and ||b||_2 (out[1]) in FP64 for a CSR system that the
+ * caller holds in device memory, computed without allocating anything.  The
+ * paper has no counterpart: this entry point is for callers that cannot call
+ * cudaMalloc -- those whose device memory was all handed to their own pool or
+ * arena up front (a service that must not hit out-of-memory mid-request) and
+ * those on a latency-critical path where cudaMalloc/cudaFree would synchronise
+ * the device.  asyrk_residual needs a problem handle, and creating one
+ * allocates; this call needs only the caller's arrays.
+ *   row_ptr (m+1 int64), col_idx (nnz int32), values (nnz of vdtype), b (m
+ *   doubles), x (n doubles) and out (2 doubles) are all DEVICE pointers, in
+ *   the plain CSR layout of asyrk_create.  Entries outside [0, nnz) and
+ *   columns outside [0, n) are not read; they make out[0] NaN.
+ *   The work is enqueued on `stream` (NULL: legacy default stream) and the
+ *   call returns without waiting: out is valid once the stream gets there.
+ * Scratch: a file-scope device array of 128 KiB + 64 B inside the library,
+ * which every GPU that loads the library holds until the process exits.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.  The first
+ * call on a device looks up that array's device address (a one-time set-up
+ * per device); make that first call before any stream capture on the device.
+ * All calls share the one array: calls whose GPU work overlaps (different
+ * streams without ordering between them) race and give wrong results; order
+ * them on one stream or wait in between.
+ * Errors: EINVAL (m < 1 or m > ASYRK_NOALLOC_MAX_ROWS -- the rows the static
+ * scratch can hold --, n outside [1, 2^31-1], nnz < 0, a NULL pointer, an
+ * unknown vdtype), ECUDA. */
+int asyrk_residual_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                           const int32_t *col_idx, const void *values, int vdtype,
+                           const double *b, const double *x, double *out, void *stream);
+
 /* Static description of a status code. */
 const char *asyrk_strerror(int status);
 

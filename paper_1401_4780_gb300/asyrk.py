@@ -69,7 +69,9 @@ class ProblemStats(ctypes.Structure):
 
 EXPORTS = ["asyrk_create", "asyrk_destroy", "asyrk_solve", "asyrk_residual", "asyrk_draw_rows",
            "asyrk_get_position", "asyrk_set_position", "asyrk_problem_get_stats",
-           "asyrk_strerror", "asyrk_last_error", "asyrk_abi_version", "asyrk_probe"]
+           "asyrk_strerror", "asyrk_last_error", "asyrk_abi_version", "asyrk_probe",
+           "asyrk_residual_noalloc"]
+NOALLOC_MAX_ROWS = 16777216
 PROBE_RED_F32, PROBE_GATHER_F32, PROBE_GATHER_RED, PROBE_STREAM = 0, 1, 2, 3
 
 _lib = None
@@ -111,6 +113,8 @@ def load(path: str = LIB_PATH):
     lib.asyrk_abi_version.restype = ctypes.c_int
     lib.asyrk_probe.argtypes = [ctypes.c_int, i64, i64, ctypes.POINTER(ctypes.c_float)]
     lib.asyrk_probe.restype = ctypes.c_int
+    lib.asyrk_residual_noalloc.argtypes = [i64, i64, i64, P, P, P, ctypes.c_int, P, P, P, P]
+    lib.asyrk_residual_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -193,6 +197,14 @@ def asyrk_probe(kind, n, ops):
     ms = ctypes.c_float()
     st = load().asyrk_probe(kind, n, ops, ctypes.byref(ms))
     return st, ms.value
+
+
+def asyrk_residual_noalloc(m, n, nnz, row_ptr, col_idx, values, vdtype, b, x, out, stream=None):
+    """Enqueue ||b - A x|| -> out[0], ||b|| -> out[1] (all device arrays); returns the status.
+
+    Allocates nothing: for callers that cannot call cudaMalloc (see asyrk.h)."""
+    return load().asyrk_residual_noalloc(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
+                                         vdtype, _ptr(b), _ptr(x), _ptr(out), _stream(stream))
 
 
 def asyrk_get_position(h):
