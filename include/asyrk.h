@@ -188,6 +188,81 @@ int asyrk_set_position(asyrk_problem *p, uint64_t j_next);
 /* Sizes and statistics of a problem.  Errors: EINVAL. */
 int asyrk_problem_get_stats(asyrk_problem *p, asyrk_problem_stats *stats);
 
+/* ------------------------------------------------------------------------
+ * Autotuner (not in the paper).  Times the projection kernel on problem p for
+ * every sub-warp width (2..32 lanes per row) and for 1/2, 3/4 and all of the
+ * resident workers (never above the Cor. 2 worker estimate m / (2 e
+ * lambda_max) - 1 with lambda_max ~ (1 + sqrt(m/n))^2, Section 1), each for
+ * `trial_projections` projections (0: min(2m, 2^22)) on a scratch iterate;
+ * the problem's row-sequence position is not changed.  The fastest shape is
+ * kept in a process-wide table keyed by (value dtype, row-length class =
+ * max_row_len rounded up to a power of two, SM count) that asyrk_solve (with
+ * subwarp = workers = 0) and asyrk_batch_create consult.  When the
+ * environment variable ASYRK_TUNE_CACHE names a file, the table is read from
+ * it on first use and rewritten after each tuning.
+ * Errors: EINVAL, ECUDA, ENOMEM.
+ * ------------------------------------------------------------------------ */
+typedef struct asyrk_tune_result {
+    int32_t subwarp;              /* chosen lanes per row                     */
+    int32_t workers;              /* chosen concurrent workers                */
+    double projections_per_s;     /* measured rate of the chosen shape        */
+    int32_t trials;               /* shapes timed                             */
+    int32_t from_cache;           /* 1: found in the table, nothing timed     */
+} asyrk_tune_result;
+
+int asyrk_autotune(asyrk_problem *p, int64_t trial_projections, int force, asyrk_tune_result *res);
+
+/* ------------------------------------------------------------------------
+ * Batched solves (not in the paper): many independent FP32/BF16 problems
+ * advanced together by one persistent projection kernel.  Each iteration
+ * splits the GPU's resident warps among the unfinished problems in proportion
+ * to their stored entries, each capped by its own Cor. 2 worker estimate, and
+ * runs one sweep of each; an FP64 check then retires the problems that met
+ * their tolerance.  With graph >= 0 the whole loop is one CUDA graph launch
+ * (a WHILE conditional node whose body is that iteration; the device stops
+ * it), else a host loop.
+ * ------------------------------------------------------------------------ */
+typedef struct asyrk_batch asyrk_batch; /* opaque; owns per-problem iterates and tables */
+
+typedef struct asyrk_batch_opts {
+    void *stream;           /* cudaStream_t; NULL = legacy default stream          */
+    int32_t graph;          /* >= 0: one graph launch per solve (default); -1: host loop */
+    int32_t row_exclusion;  /* as in asyrk_solve_opts                               */
+} asyrk_batch_opts;
+
+typedef struct asyrk_batch_info {
+    int32_t status;           /* OK if all converged, else the worst status        */
+    int32_t converged;        /* problems that met their tolerance                 */
+    int64_t iterations;       /* engine iterations (sweeps of the longest solve)   */
+    int64_t projections;      /* projections over all problems                     */
+    double seconds;           /* wall time of the call                             */
+    double device_ms;         /* CUDA-event time of the iteration loop             */
+    int64_t kernel_launches;  /* kernels run by the call (graph nodes included)    */
+    int32_t resident_warps;   /* warps the engine splits among the problems        */
+    int32_t graph;            /* 1: the loop ran as one graph launch               */
+} asyrk_batch_info;
+
+/* Group `count` problems (FP32 or BF16 values, all on the current device, each
+ * at most once; count <= the resident warps, several thousand on a GB300).
+ * The problems must outlive the batch.  Errors: EINVAL, ENOMEM, ECUDA. */
+int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *problems, int count,
+                       const asyrk_batch_opts *opts);
+
+/* Solve every member from xs[k] (in: x0, out: x; n_k doubles each, host or
+ * device per device_ptrs) with step length gammas[k] (NULL: all 1) to
+ * tols[k] (NULL: run max_sweeps sweeps), measured as ||x-x*||/||x*|| when
+ * x_trues[k] is given (x_trues or an entry may be NULL) else ||b-Ax||/||b||;
+ * at most max_sweeps sweeps each.  infos (count entries, may be NULL) get
+ * each problem's outcome; rel_res is the final FP64 ||b - A x||/||b||.  Each
+ * problem's row sequence continues from its position, which advances.
+ * Returns OK when all converged, else the worst status (NOT_CONVERGED,
+ * DIVERGED), or EINVAL / ECUDA. */
+int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double *gammas, const double *tols,
+                      int64_t max_sweeps, const double *const *x_trues, int device_ptrs,
+                      asyrk_solve_info *infos, asyrk_batch_info *binfo);
+
+void asyrk_batch_destroy(asyrk_batch *b);
+
 /* Largest m accepted by asyrk_residual_noalloc. */
 #define ASYRK_NOALLOC_MAX_ROWS 16777216
 

@@ -70,7 +70,8 @@ class ProblemStats(ctypes.Structure):
 EXPORTS = ["asyrk_create", "asyrk_destroy", "asyrk_solve", "asyrk_residual", "asyrk_draw_rows",
            "asyrk_get_position", "asyrk_set_position", "asyrk_problem_get_stats",
            "asyrk_strerror", "asyrk_last_error", "asyrk_abi_version", "asyrk_probe",
-           "asyrk_residual_noalloc"]
+           "asyrk_residual_noalloc", "asyrk_autotune", "asyrk_batch_create", "asyrk_batch_solve",
+           "asyrk_batch_destroy"]
 NOALLOC_MAX_ROWS = 16777216
 PROBE_RED_F32, PROBE_GATHER_F32, PROBE_GATHER_RED, PROBE_STREAM = 0, 1, 2, 3
 
@@ -115,8 +116,43 @@ def load(path: str = LIB_PATH):
     lib.asyrk_probe.restype = ctypes.c_int
     lib.asyrk_residual_noalloc.argtypes = [i64, i64, i64, P, P, P, ctypes.c_int, P, P, P, P]
     lib.asyrk_residual_noalloc.restype = ctypes.c_int
+    lib.asyrk_autotune.argtypes = [P, i64, ctypes.c_int, ctypes.POINTER(TuneResult)]
+    lib.asyrk_autotune.restype = ctypes.c_int
+    lib.asyrk_batch_create.argtypes = [ctypes.POINTER(P), P, ctypes.c_int,
+                                       ctypes.POINTER(BatchOpts)]
+    lib.asyrk_batch_create.restype = ctypes.c_int
+    lib.asyrk_batch_solve.argtypes = [P, P, P, P, i64, P, ctypes.c_int, P,
+                                      ctypes.POINTER(BatchInfo)]
+    lib.asyrk_batch_solve.restype = ctypes.c_int
+    lib.asyrk_batch_destroy.argtypes = [P]
+    lib.asyrk_batch_destroy.restype = None
     _lib = lib
     return lib
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("subwarp", ctypes.c_int32), ("workers", ctypes.c_int32),
+                ("projections_per_s", ctypes.c_double), ("trials", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("graph", ctypes.c_int32),
+                ("row_exclusion", ctypes.c_int32)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("iterations", ctypes.c_int64), ("projections", ctypes.c_int64),
+                ("seconds", ctypes.c_double), ("device_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("resident_warps", ctypes.c_int32),
+                ("graph", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def _ptr(a):
@@ -205,6 +241,47 @@ def asyrk_residual_noalloc(m, n, nnz, row_ptr, col_idx, values, vdtype, b, x, ou
     Allocates nothing: for callers that cannot call cudaMalloc (see asyrk.h)."""
     return load().asyrk_residual_noalloc(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
                                          vdtype, _ptr(b), _ptr(x), _ptr(out), _stream(stream))
+
+
+def asyrk_autotune(h, trial_projections=0, force=False):
+    r = TuneResult()
+    st = load().asyrk_autotune(h, trial_projections, 1 if force else 0, ctypes.byref(r))
+    return st, r
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for k, a in enumerate(items):
+        p = _ptr(a)
+        arr[k] = None if p is None else (p.value if isinstance(p, ctypes.c_void_p) else p)
+    return arr
+
+
+def asyrk_batch_create(handles, stream=None, graph=True, row_exclusion=0):
+    b = ctypes.c_void_p()
+    hs = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    o = BatchOpts(stream=_stream(stream), graph=0 if graph else -1, row_exclusion=row_exclusion)
+    st = load().asyrk_batch_create(ctypes.byref(b), hs, len(handles), ctypes.byref(o))
+    return st, b
+
+
+def asyrk_batch_solve(b, xs, gammas=None, tols=None, max_sweeps=1000, x_trues=None,
+                      device_ptrs=False):
+    """xs updated in place; returns (status, [SolveInfo], BatchInfo)."""
+    n = len(xs)
+    xa = _ptr_array(xs)
+    ga = None if gammas is None else np.ascontiguousarray(gammas, dtype=np.float64)
+    ta = None if tols is None else np.ascontiguousarray(tols, dtype=np.float64)
+    xt = None if x_trues is None else _ptr_array(x_trues)
+    infos = (SolveInfo * n)()
+    bi = BatchInfo()
+    st = load().asyrk_batch_solve(b, xa, _ptr(ga), _ptr(ta), int(max_sweeps), xt,
+                                  1 if device_ptrs else 0, infos, ctypes.byref(bi))
+    return st, list(infos), bi
+
+
+def asyrk_batch_destroy(b):
+    load().asyrk_batch_destroy(b)
 
 
 def asyrk_get_position(h):
@@ -302,3 +379,46 @@ class Problem:
 
     def stats(self):
         return asyrk_problem_get_stats(self.h)[1].as_dict()
+
+    def autotune(self, trial_projections=0, force=False):
+        st, r = asyrk_autotune(self.h, trial_projections, force)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_autotune")
+        return r
+
+
+class Batch:
+    """Owns one asyrk_batch handle over a list of Problem objects."""
+
+    def __init__(self, problems, stream=None, graph=True, row_exclusion=0):
+        self.problems = list(problems)
+        st, b = asyrk_batch_create([p.h for p in self.problems], stream=stream, graph=graph,
+                                   row_exclusion=row_exclusion)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_batch_create")
+        self.b = b
+
+    def solve(self, xs, gammas=None, tols=None, max_sweeps=1000, x_trues=None,
+              device_ptrs=False, raise_on_error=True):
+        st, infos, bi = asyrk_batch_solve(self.b, xs, gammas, tols, max_sweeps, x_trues,
+                                          device_ptrs)
+        if st < 0 and raise_on_error:
+            raise AsyrkError(st, "asyrk_batch_solve")
+        return st, infos, bi
+
+    def close(self):
+        if self.b is not None and self.b.value:
+            asyrk_batch_destroy(self.b)
+        self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,86 @@
+// batch.cuh -- many independent systems ("slots") advanced by one persistent
+// projection kernel, shared by the batched solve (batch.cu) and the server
+// (server.cu).
+//
+// One iteration of the engine is four kernels:
+//   plan     split the resident warps among the active slots in proportion to
+//            their work per sweep, each capped by its concurrency limit (the
+//            tau bound of Cor. 2, expressed in warps);
+//   project  every warp finds its slot and runs that slot's workers for one
+//            sweep (m_s projections) with the slot's value type and sub-warp
+//            width (worker.cuh);
+//   check    the slot's FP64 error measure (||x - x*|| / ||x*|| with x*, else
+//            ||b - A x|| / ||b||), its sweep count and done/status;
+//   cond     count the active slots; in a CUDA graph, set the WHILE condition.
+#pragma once
+
+#include "common.cuh"
+
+namespace asyrk {
+
+constexpr int BATCH_ERR_CHUNK = 16384;  // x entries per check block (x* measure)
+constexpr int BATCH_ROW_CHUNK = 2048;   // rows per check block (residual measure)
+
+struct SysDesc {
+    const RowRec *rec;
+    const int32_t *col;
+    const void *val;
+    const double *b64;  // FP64 b of the problem (final residual)
+    const float *bvec;  // FP32 right-hand side replacing rec.b, or nullptr
+    float *x;           // FP32 iterate of this slot
+    double *x64;        // FP64 staging of this slot's x (in/out)
+    const double *xt;   // x* in FP64, or nullptr: residual measure
+    unsigned *busy;     // row-claim bits of this slot
+    double ref;         // ||x*|| or ||b||; < 0: computed by the first check
+    double tol;
+    double meas;        // last check measure
+    double meas0;       // first measure (divergence test)
+    double res2, bb2;   // final FP64 ||b - A x||^2 and ||b||^2
+    double work;        // stored entries per sweep
+    unsigned long long j;        // next projection of the slot's row sequence
+    unsigned long long skipped;  // projections skipped by row exclusion
+    long long sweeps;
+    long long max_sweeps;
+    uint2 key;
+    unsigned m, n;
+    unsigned stream_id;
+    float gamma;
+    int dtype;
+    int G;
+    int cap_warps;  // concurrency cap in warps
+    int uniform;
+    int active;     // 1 while being solved
+    int status;
+    int warp0, nwarps;    // this iteration's warps
+    int first_nwarps;     // warps of the first iteration (reported)
+    int chunk0, nchunks;  // check blocks of this slot
+    unsigned chk_count;   // last-block counter of the check
+    unsigned res_count;   // last-block counter of the final residual
+};
+
+// warps of the project kernel that are resident on the whole GPU at once
+int batch_resident_warps(int sm_count, bool excl, int *warps);
+
+// One engine iteration (plan, project, check, cond) enqueued on s.  d_iter[0]
+// counts iterations, d_iter[1] bounds them; d_active receives the active slots.
+// use_cond: call cudaGraphSetConditional(h, ...) (only inside a graph).
+int launch_batch_iteration(SysDesc *d, int count, int total_chunks, double *part,
+                           int resident_warps, bool excl, int *d_active, int *d_iter,
+                           bool use_cond, unsigned long long cond_handle, cudaStream_t s);
+
+// The check alone with measure_only: first measure (and ||x*||), no sweep.
+int launch_batch_measure(SysDesc *d, int count, int total_chunks, double *part, cudaStream_t s);
+
+// Final FP64 residual of every slot from its x64 staging (res2, bb2).
+int launch_batch_residual(SysDesc *d, int count, int total_chunks, double *part, cudaStream_t s);
+
+// x64 <-> x conversions over all slots (n_total entries laid out slot by slot)
+int launch_batch_convert(const double *x64, float *x, int64_t n_total, bool to_f32, cudaStream_t s);
+
+long long tau_cap_estimate(int64_t m, int64_t n);
+
+// autotuned (sub-warp width, fraction of the resident workers) for problems of
+// this value dtype and row-length class on this GPU, if asyrk_autotune ran
+bool tuned_shape(int dtype, int64_t max_len, int *G, double *frac);
+
+}  // namespace asyrk

@@ -1,0 +1,407 @@
+// engine.cu -- kernels of the multi-system engine (see batch.cuh).
+#include <math.h>
+
+#include "batch.cuh"
+#include "worker.cuh"
+
+namespace asyrk {
+
+// Cor. 2 asks 2 e lambda_max (tau + 1) / m <= 1 for near-linear speedup.  With
+// no lambda_max at hand the estimate uses Section 1's value for row-normalised
+// Gaussian matrices, lambda_max ~ (1 + sqrt(m/n))^2.
+long long tau_cap_estimate(int64_t m, int64_t n)
+{
+    const double ratio = (double)m / (double)n;
+    const double lmax = (1.0 + sqrt(ratio)) * (1.0 + sqrt(ratio));
+    const double cap = (double)m / (2.0 * M_E * lmax) - 1.0;
+    return cap < 1.0 ? 1LL : (long long)cap;
+}
+
+// ---------------------------------------------------------------------------
+// plan: one thread; a handful of passes over the slots
+// ---------------------------------------------------------------------------
+__global__ void k_batch_plan(SysDesc *d, int count, int R)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double wtot = 0.0;
+    for (int s = 0; s < count; ++s)
+        if (d[s].active) wtot += d[s].work;
+    int used = 0;
+    for (int s = 0; s < count; ++s) {
+        int w = 0;
+        if (d[s].active && wtot > 0.0) {
+            w = (int)((double)R * d[s].work / wtot);
+            if (w < 1) w = 1;
+            if (w > d[s].cap_warps) w = d[s].cap_warps;
+        }
+        d[s].nwarps = w;
+        used += w;
+    }
+    // hand the remainder to slots below their cap, in proportion to their work
+    for (int pass = 0; pass < 2 && used < R; ++pass) {
+        double wunc = 0.0;
+        for (int s = 0; s < count; ++s)
+            if (d[s].active && d[s].nwarps < d[s].cap_warps) wunc += d[s].work;
+        if (wunc <= 0.0) break;
+        const int left = R - used;
+        for (int s = 0; s < count && used < R; ++s) {
+            if (!d[s].active || d[s].nwarps >= d[s].cap_warps) continue;
+            int add = (int)((double)left * d[s].work / wunc);
+            if (add > d[s].cap_warps - d[s].nwarps) add = d[s].cap_warps - d[s].nwarps;
+            if (add > R - used) add = R - used;
+            d[s].nwarps += add;
+            used += add;
+        }
+    }
+    int acc = 0;
+    for (int s = 0; s < count; ++s) {
+        if (acc + d[s].nwarps > R) d[s].nwarps = R - acc > 0 ? R - acc : 0;
+        d[s].warp0 = acc;
+        acc += d[s].nwarps;
+        if (d[s].first_nwarps == 0) d[s].first_nwarps = d[s].nwarps;
+    }
+}
+
+// largest slot index whose start (warp0 or chunk0) is <= key
+__device__ __forceinline__ int find_slot_warp(const SysDesc *d, int count, int key)
+{
+    int lo = 0, hi = count - 1, s = -1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        if (d[mid].warp0 <= key) {
+            s = mid;
+            lo = mid + 1;
+        } else {
+            hi = mid - 1;
+        }
+    }
+    return s;
+}
+
+__device__ __forceinline__ int find_slot_chunk(const SysDesc *d, int count, int key)
+{
+    int lo = 0, hi = count - 1, s = -1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        if (d[mid].chunk0 <= key) {
+            s = mid;
+            lo = mid + 1;
+        } else {
+            hi = mid - 1;
+        }
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// project: one sweep of every active slot
+// ---------------------------------------------------------------------------
+template <typename VT, int G, bool EXCL>
+__device__ __forceinline__ unsigned long long batch_run(const ProjArgs &a, int rel_warp)
+{
+    return run_workers<VT, float, G, false, EXCL>(a, (long long)rel_warp * (32 / G), a.workers);
+}
+
+template <typename VT, bool EXCL>
+__device__ __forceinline__ unsigned long long batch_run_g(const ProjArgs &a, int G, int rel_warp)
+{
+    switch (G) {
+    case 2: return batch_run<VT, 2, EXCL>(a, rel_warp);
+    case 4: return batch_run<VT, 4, EXCL>(a, rel_warp);
+    case 8: return batch_run<VT, 8, EXCL>(a, rel_warp);
+    case 16: return batch_run<VT, 16, EXCL>(a, rel_warp);
+    default: return batch_run<VT, 32, EXCL>(a, rel_warp);
+    }
+}
+
+template <bool EXCL>
+__global__ void __launch_bounds__(256) k_batch_project(SysDesc *d, int count)
+{
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int s = find_slot_warp(d, count, gw);
+    if (s < 0) return;
+    const SysDesc &D = d[s];
+    if (!D.active || gw >= D.warp0 + D.nwarps) return;  // warp-uniform
+    ProjArgs a;
+    a.rec = D.rec;
+    a.col = D.col;
+    a.val = D.val;
+    a.x = D.x;
+    a.b64 = nullptr;
+    a.w64 = nullptr;
+    a.key = D.key;
+    a.m = D.m;
+    a.uniform = D.uniform;
+    a.stream_id = D.stream_id;
+    a.j0 = D.j;
+    a.count = D.m;  // one sweep
+    a.workers = (long long)D.nwarps * (32 / D.G);
+    a.gamma = (double)D.gamma;
+    a.bvec = D.bvec;
+    a.busy = D.busy;
+    a.skipped = nullptr;
+    const int rel = gw - D.warp0;
+    const unsigned long long sk = (D.dtype == ASYRK_BF16)
+                                      ? batch_run_g<bf16_t, EXCL>(a, D.G, rel)
+                                      : batch_run_g<float, EXCL>(a, D.G, rel);
+    if (EXCL && sk) atomicAdd(&d[s].skipped, sk);
+}
+
+// ---------------------------------------------------------------------------
+// block reduction of two doubles; returns true in thread 0 of the last block
+// of the slot to finish (which then holds the slot's totals in t0, t1)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool slot_reduce(double v0, double v1, double *part, int chunk,
+                                            int chunk0, int nchunks, unsigned *counter,
+                                            double &t0, double &t1)
+{
+    __shared__ double sh[2][8];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
+    if (lane == 0) {
+        sh[0][wid] = v0;
+        sh[1][wid] = v1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+        part[2 * chunk] = a;
+        part[2 * chunk + 1] = b;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == (unsigned)nchunks - 1u);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nchunks; k += 256) {
+        a += __ldcg(part + 2 * (chunk0 + k));
+        b += __ldcg(part + 2 * (chunk0 + k) + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sh[0][wid] = a;
+        sh[1][wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return false;
+    t0 = 0.0;
+    t1 = 0.0;
+    for (int w = 0; w < 8; ++w) {
+        t0 += sh[0][w];
+        t1 += sh[1][w];
+    }
+    *counter = 0u;
+    return true;
+}
+
+__device__ __forceinline__ double slot_value(int dtype, const void *val, long long k)
+{
+    if (dtype == ASYRK_BF16)
+        return (double)__uint_as_float(((unsigned)static_cast<const bf16_t *>(val)[k].bits) << 16);
+    return (double)static_cast<const float *>(val)[k];
+}
+
+// measure_only: the first measure before any sweep (also ||x*|| when ref < 0)
+__global__ void __launch_bounds__(256) k_batch_check(SysDesc *d, int count, double *part,
+                                                     int measure_only)
+{
+    const int c = blockIdx.x;
+    const int s = find_slot_chunk(d, count, c);
+    if (s < 0) return;
+    SysDesc &D = d[s];
+    if (c >= D.chunk0 + D.nchunks) return;
+    if (!D.active || (!measure_only && D.nwarps == 0)) return;  // same for all blocks of s
+    const int k = c - D.chunk0;
+    double v0 = 0.0, v1 = 0.0;
+    if (D.xt) {
+        const long long lo = (long long)k * BATCH_ERR_CHUNK;
+        long long hi = lo + BATCH_ERR_CHUNK;
+        if (hi > D.n) hi = D.n;
+        for (long long t = lo + threadIdx.x; t < hi; t += 256) {
+            const double e = (double)__ldcg(D.x + t) - D.xt[t];
+            v0 += e * e;
+            v1 += D.xt[t] * D.xt[t];
+        }
+    } else {
+        const long long lo = (long long)k * BATCH_ROW_CHUNK;
+        long long hi = lo + BATCH_ROW_CHUNK;
+        if (hi > D.m) hi = D.m;
+        for (long long i = lo + threadIdx.x; i < hi; i += 256) {
+            const RowRec r = D.rec[i];
+            double acc = 0.0;
+            for (unsigned q = 0; q < r.len; ++q)
+                acc += slot_value(D.dtype, D.val, r.start + q) *
+                       (double)__ldcg(D.x + D.col[r.start + q]);
+            const double bi = D.bvec ? (double)D.bvec[i] : (double)r.b;
+            const double ri = bi - acc;
+            v0 += ri * ri;
+            v1 += bi * bi;
+        }
+    }
+    double t0, t1;
+    if (!slot_reduce(v0, v1, part, c, D.chunk0, D.nchunks, &D.chk_count, t0, t1)) return;
+    if (D.ref < 0.0) D.ref = sqrt(t1) > 0.0 ? sqrt(t1) : 1.0;
+    const double meas = sqrt(t0) / D.ref;
+    D.meas = meas;
+    if (measure_only) {
+        D.meas0 = meas;
+        if (meas <= D.tol) {
+            D.active = 0;
+            D.status = ASYRK_OK;
+        } else if (D.max_sweeps <= 0) {
+            D.active = 0;
+            D.status = ASYRK_NOT_CONVERGED;
+        }
+        return;
+    }
+    D.j += D.m;
+    D.sweeps += 1;
+    if (!isfinite(meas) || meas > 1e30 * (D.meas0 > 0.0 ? D.meas0 : 1.0)) {
+        D.active = 0;
+        D.status = ASYRK_DIVERGED;
+    } else if (meas <= D.tol) {
+        D.active = 0;
+        D.status = ASYRK_OK;
+    } else if (D.sweeps >= D.max_sweeps) {
+        D.active = 0;
+        D.status = ASYRK_NOT_CONVERGED;
+    }
+}
+
+// final ||b - A x64|| and ||b|| in FP64 per slot (row chunks)
+__global__ void __launch_bounds__(256) k_batch_residual(SysDesc *d, int count, double *part)
+{
+    const int c = blockIdx.x;
+    const int s = find_slot_chunk(d, count, c);
+    if (s < 0) return;
+    SysDesc &D = d[s];
+    if (c >= D.chunk0 + D.nchunks) return;
+    const int k = c - D.chunk0;
+    double v0 = 0.0, v1 = 0.0;
+    const long long lo = (long long)k * BATCH_ROW_CHUNK;
+    long long hi = lo + BATCH_ROW_CHUNK;
+    if (hi > D.m) hi = D.m;
+    for (long long i = lo + threadIdx.x; i < hi; i += 256) {
+        const RowRec r = D.rec[i];
+        double acc = 0.0;
+        for (unsigned q = 0; q < r.len; ++q)
+            acc += slot_value(D.dtype, D.val, r.start + q) * D.x64[D.col[r.start + q]];
+        const double ri = D.b64[i] - acc;
+        v0 += ri * ri;
+        v1 += D.b64[i] * D.b64[i];
+    }
+    double t0, t1;
+    if (!slot_reduce(v0, v1, part, c, D.chunk0, D.nchunks, &D.res_count, t0, t1)) return;
+    D.res2 = t0;
+    D.bb2 = t1;
+}
+
+// d_iter[0]: iterations done, d_iter[1]: the iteration bound
+__global__ void k_batch_cond(SysDesc *d, int count, int *d_active, int *d_iter, int use_cond,
+                             cudaGraphConditionalHandle h)
+{
+    __shared__ int sh[8];
+    int a = 0;
+    for (int s = threadIdx.x; s < count; s += blockDim.x) a += d[s].active;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+        *d_active = tot;
+        const int it = d_iter[0] + 1;
+        d_iter[0] = it;
+        if (use_cond) cudaGraphSetConditional(h, (tot > 0 && it < d_iter[1]) ? 1u : 0u);
+    }
+}
+
+__global__ void k_batch_convert(const double *x64, float *x, int64_t n, int to_f32, double *out64,
+                                const float *in32)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (to_f32)
+            x[i] = (float)x64[i];
+        else
+            out64[i] = (double)in32[i];
+    }
+}
+
+int batch_resident_warps(int sm_count, bool excl, int *warps)
+{
+    int per_sm = 0;
+    if (excl)
+        ASYRK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_project<true>, 256, 0));
+    else
+        ASYRK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_project<false>, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    *warps = per_sm * sm_count * 8;
+    return ASYRK_OK;
+}
+
+int launch_batch_iteration(SysDesc *d, int count, int total_chunks, double *part,
+                           int resident_warps, bool excl, int *d_active, int *d_iter,
+                           bool use_cond, unsigned long long cond_handle, cudaStream_t s)
+{
+    k_batch_plan<<<1, 32, 0, s>>>(d, count, resident_warps);
+    ASYRK_CK(cudaGetLastError());
+    const unsigned blocks = (unsigned)((resident_warps + 7) / 8);
+    if (excl)
+        k_batch_project<true><<<blocks, 256, 0, s>>>(d, count);
+    else
+        k_batch_project<false><<<blocks, 256, 0, s>>>(d, count);
+    ASYRK_CK(cudaGetLastError());
+    k_batch_check<<<(unsigned)total_chunks, 256, 0, s>>>(d, count, part, 0);
+    ASYRK_CK(cudaGetLastError());
+    k_batch_cond<<<1, 256, 0, s>>>(d, count, d_active, d_iter, use_cond ? 1 : 0,
+                                   (cudaGraphConditionalHandle)cond_handle);
+    ASYRK_CK(cudaGetLastError());
+    return ASYRK_OK;
+}
+
+int launch_batch_measure(SysDesc *d, int count, int total_chunks, double *part, cudaStream_t s)
+{
+    k_batch_check<<<(unsigned)total_chunks, 256, 0, s>>>(d, count, part, 1);
+    ASYRK_CK(cudaGetLastError());
+    return ASYRK_OK;
+}
+
+int launch_batch_residual(SysDesc *d, int count, int total_chunks, double *part, cudaStream_t s)
+{
+    k_batch_residual<<<(unsigned)total_chunks, 256, 0, s>>>(d, count, part);
+    ASYRK_CK(cudaGetLastError());
+    return ASYRK_OK;
+}
+
+int launch_batch_convert(const double *x64, float *x, int64_t n_total, bool to_f32, cudaStream_t s)
+{
+    int64_t g = (n_total + 255) / 256;
+    if (g > 8192) g = 8192;
+    if (g < 1) g = 1;
+    if (to_f32)
+        k_batch_convert<<<(unsigned)g, 256, 0, s>>>(x64, x, n_total, 1, nullptr, nullptr);
+    else
+        k_batch_convert<<<(unsigned)g, 256, 0, s>>>(nullptr, nullptr, n_total, 0,
+                                                    const_cast<double *>(x64), x);
+    ASYRK_CK(cudaGetLastError());
+    return ASYRK_OK;
+}
+
+}  // namespace asyrk

@@ -15,7 +15,7 @@
 
 #include <chrono>
 
-#include "common.cuh"
+#include "batch.cuh"
 
 namespace asyrk {
 
@@ -25,16 +25,7 @@ static double now_s()
         .count();
 }
 
-// Cor. 2 asks 2 e lambda_max (tau + 1) / m <= 1 for near-linear speedup.  With
-// no lambda_max at hand the automatic worker count uses Section 1's estimate
-// for row-normalised Gaussian matrices, lambda_max ~ (1 + sqrt(m/n))^2.
-static long long tau_cap(const asyrk_problem *p)
-{
-    const double ratio = (double)p->m / (double)p->n;
-    const double lmax = (1.0 + sqrt(ratio)) * (1.0 + sqrt(ratio));
-    const double cap = (double)p->m / (2.0 * M_E * lmax) - 1.0;
-    return cap < 1.0 ? 1LL : (long long)cap;
-}
+static long long tau_cap(const asyrk_problem *p) { return tau_cap_estimate(p->m, p->n); }
 
 struct SolveCtx {
     asyrk_problem *p;
@@ -108,6 +99,10 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
     const bool seq = o.mode == ASYRK_MODE_SEQUENTIAL;
     const bool x_f64 = seq || p->dtype == ASYRK_F64;
     int G = o.subwarp ? o.subwarp : choose_subwarp(p->max_len, p->nnz, p->m);
+    double frac = 1.0;
+    int tG = 0;
+    if (!seq && o.subwarp == 0 && o.workers == 0 && tuned_shape(p->dtype, p->max_len, &tG, &frac))
+        G = tG;  // the autotuner's shape for this kind of problem
     long long W = 1;
     if (!seq) {
         int maxw = 0;
@@ -116,7 +111,8 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
         if (o.workers > 0) {
             W = o.workers;
         } else {
-            W = maxw;
+            W = (long long)(frac * maxw);
+            if (W < 1) W = 1;
             const long long cap = tau_cap(p);
             if (W > cap) W = cap;
         }
@@ -175,11 +171,15 @@ static int solve_refine(SolveCtx &c, double gamma, double tol, int64_t max_sweep
                         const asyrk_solve_opts &o, asyrk_solve_info &info)
 {
     asyrk_problem *p = c.p;
-    const int G = o.subwarp ? o.subwarp : choose_subwarp(p->max_len, p->nnz, p->m);
+    int G = o.subwarp ? o.subwarp : choose_subwarp(p->max_len, p->nnz, p->m);
+    double frac = 1.0;
+    int tG = 0;
+    if (o.subwarp == 0 && o.workers == 0 && tuned_shape(p->dtype, p->max_len, &tG, &frac)) G = tG;
     int maxw = 0;
     int st = project_max_workers(p, false, G, &maxw);
     if (st != ASYRK_OK) return st;
-    long long W = o.workers > 0 ? o.workers : maxw;
+    long long W = o.workers > 0 ? o.workers : (long long)(frac * maxw);
+    if (W < 1) W = 1;
     if (o.workers <= 0 && W > tau_cap(p)) W = tau_cap(p);
     info.workers = (int32_t)W;
     info.subwarp = G;

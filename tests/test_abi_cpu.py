@@ -49,6 +49,9 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(asyrk.SolveOpts) == 64
     assert ctypes.sizeof(asyrk.SolveInfo) == 96
     assert ctypes.sizeof(asyrk.ProblemStats) == 80
+    assert ctypes.sizeof(asyrk.BatchOpts) == 16
+    assert ctypes.sizeof(asyrk.BatchInfo) == 56
+    assert ctypes.sizeof(asyrk.TuneResult) == 24
 
 
 def test_abi_version_and_status_strings(lib):

@@ -1,0 +1,127 @@
+"""Batched solves (many independent systems in one graph launch) and the autotuner.
+
+  * uneven FP32/BF16 systems (m from 2^11 to 2^14, n = m/4, 8..64 entries per
+    row, unit rows) reach ||x-x*||/||x*|| <= 1e-6 each, checked on the host,
+    within 1.5x the oracle's median sweep count for that system;
+  * each system's result is the same alone (asyrk_solve) and in the mix, within
+    the tolerance: both are within 1e-6 of x*;
+  * the graph launch and the host loop agree; the residual measure works
+    without x*; the sweep budget gives NOT_CONVERGED; bad batches are rejected;
+  * the autotuner returns a shape the solve then uses.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_4780_gb300 import asyrk, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    asyrk.load()
+
+
+def _systems():
+    shapes = [(2048, 512, 8), (3000, 750, 64), (4096, 1024, 16), (6000, 1500, 33),
+              (8192, 2048, 40), (12000, 3000, 12), (16384, 4096, 24), (2500, 625, 57)]
+    out = []
+    for k, (m, n, L) in enumerate(shapes):
+        dt = "bf16" if k % 4 == 3 else "f32"
+        out.append(synth.make_system(m, n, L, 500 + k, row_norms="unit", value_dtype=dt))
+    return out
+
+
+def _err(x, s):
+    return np.linalg.norm(x - s.x_true) / np.linalg.norm(s.x_true)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_reaches_tolerance_within_oracle_sweeps(graph):
+    systems = _systems()
+    probs = [asyrk.Problem.from_system(s) for s in systems]
+    with asyrk.Batch(probs, graph=graph) as b:
+        xs = [np.zeros(s.n) for s in systems]
+        st, infos, bi = b.solve(xs, tols=[1e-6] * len(systems), max_sweeps=400,
+                                x_trues=[s.x_true for s in systems])
+        assert st == asyrk.OK, [i.status for i in infos]
+        assert bi.converged == len(systems) and bi.graph == (1 if graph else 0)
+        assert bi.iterations == max(i.sweeps for i in infos)
+    for s, x, info in zip(systems, xs, infos):
+        assert _err(x, s) <= 1e-6 and abs(info.rel_err - _err(x, s)) <= 1e-3 * _err(x, s)
+        assert info.rel_res < 1e-5
+        sweeps = []
+        for k in range(3):
+            xo = np.zeros(s.n)
+            r = oracle.rk_solve(s.m, s.n, s.row_ptr, s.col, s.val64, s.b, xo, 1.0,
+                                synth.solver_seed(s.seed) + k, 1e-6, 400, x_true=s.x_true)
+            sweeps.append(r.sweeps)
+        assert info.sweeps <= 1.5 * np.median(sweeps), (s.m, info.sweeps, sweeps)
+    for p in probs:
+        p.close()
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix():
+    systems = _systems()
+    probs = [asyrk.Problem.from_system(s) for s in systems]
+    alone = []
+    for s, p in zip(systems, probs):
+        x = np.zeros(s.n)
+        st, info = p.solve(x, tol=1e-6, max_sweeps=400, x_true=s.x_true)
+        assert st == asyrk.OK
+        alone.append(x)
+    with asyrk.Batch(probs) as b:
+        mix = [np.zeros(s.n) for s in systems]
+        st, infos, _ = b.solve(mix, tols=[1e-6] * len(systems), max_sweeps=400,
+                               x_trues=[s.x_true for s in systems])
+        assert st == asyrk.OK
+    for s, xa, xm in zip(systems, alone, mix):
+        assert _err(xa, s) <= 1e-6 and _err(xm, s) <= 1e-6
+        assert np.linalg.norm(xa - xm) / np.linalg.norm(s.x_true) <= 2e-6
+    for p in probs:
+        p.close()
+
+
+def test_batch_residual_measure_and_budget():
+    systems = _systems()[:4]
+    probs = [asyrk.Problem.from_system(s) for s in systems]
+    with asyrk.Batch(probs) as b:
+        xs = [np.zeros(s.n) for s in systems]
+        st, infos, _ = b.solve(xs, tols=[1e-5] * 4, max_sweeps=400)  # ||b - Ax||/||b||
+        assert st == asyrk.OK
+        for info in infos:
+            assert info.rel_err == -1.0 and info.rel_res <= 1.2e-5
+        xs = [np.zeros(s.n) for s in systems]
+        st, infos, bi = b.solve(xs, tols=[1e-12] * 4, max_sweeps=3,
+                                x_trues=[s.x_true for s in systems])
+        assert st == asyrk.NOT_CONVERGED and bi.converged == 0
+        assert all(i.sweeps == 3 and i.status == asyrk.NOT_CONVERGED for i in infos)
+    for p in probs:
+        p.close()
+
+
+def test_bad_batches_are_rejected():
+    s64 = synth.make_system(1024, 256, 8, 1, value_dtype="f64")
+    s32 = synth.make_system(1024, 256, 8, 2, value_dtype="f32")
+    with asyrk.Problem.from_system(s64) as p64, asyrk.Problem.from_system(s32) as p32:
+        assert asyrk.asyrk_batch_create([p64.h])[0] == asyrk.EINVAL
+        assert asyrk.asyrk_batch_create([p32.h, p32.h])[0] == asyrk.EINVAL
+        assert asyrk.asyrk_batch_create([])[0] == asyrk.EINVAL
+
+
+def test_autotune_shape_is_used_by_solve():
+    s = synth.make_system(1 << 16, 1 << 14, 24, 11, row_norms="lognormal", value_dtype="f32")
+    with asyrk.Problem.from_system(s) as p:
+        r = p.autotune(force=True)
+        assert r.subwarp in (2, 4, 8, 16, 32) and r.workers >= 1 and r.trials >= 2
+        assert r.projections_per_s > 0 and r.from_cache == 0
+        assert p.position == 0  # tuning does not move the row sequence
+        r2 = p.autotune()
+        assert r2.from_cache == 1 and r2.subwarp == r.subwarp
+        x = np.zeros(s.n)
+        st, info = p.solve(x, tol=1e-5, max_sweeps=400, x_true=s.x_true)
+        assert st == asyrk.OK and info.subwarp == r.subwarp
