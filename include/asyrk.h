@@ -64,6 +64,7 @@ typedef enum asyrk_status {
     ASYRK_ENOMEM = -2,        /* device or host allocation failed           */
     ASYRK_ECUDA = -3,         /* a CUDA call failed                         */
     ASYRK_ETIMEOUT = -4,      /* a bounded wait gave up                     */
+    ASYRK_ECANCELED = -5,     /* a served request was cancelled             */
     ASYRK_NOT_CONVERGED = 1,  /* max_sweeps reached above the tolerance     */
     ASYRK_DIVERGED = 2        /* the error measure became non-finite/huge   */
 } asyrk_status;
@@ -262,6 +263,75 @@ int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double *gammas, c
                       asyrk_solve_info *infos, asyrk_batch_info *binfo);
 
 void asyrk_batch_destroy(asyrk_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Served solves (not in the paper): continuous batching.  Requests name a
+ * resident problem (FP32 or BF16 values) and bring x0, optionally x*, gamma,
+ * a tolerance and a mode: ASYNC (FP32 iterate) or REFINE (FP64 iterate, each
+ * outer step r = b - A x in FP64 then an FP32 inner solve of A d = r to a
+ * relative residual of inner_tol).  An engine thread admits queued requests
+ * into free slots while the device-memory budget allows -- each request's
+ * iterate, staging, claim bits and residual, plus its problem's bytes counted
+ * once while any request uses it -- and advances all admitted requests
+ * together, one sweep of each per engine step in one persistent kernel
+ * launch; a request that finishes frees its slot for the next.  Each request
+ * draws its own row sequence (Philox stream = its ticket), so one problem can
+ * serve several requests at once.  The problems must outlive their requests;
+ * the server must outlive every wait on it.
+ * ------------------------------------------------------------------------ */
+typedef struct asyrk_server asyrk_server; /* opaque */
+
+typedef struct asyrk_server_opts {
+    int64_t mem_budget_bytes;  /* device bytes admitted requests may hold (> 0)      */
+    int32_t max_slots;         /* requests in flight at once (0: 256)                */
+    int32_t row_exclusion;     /* as in asyrk_solve_opts                             */
+    double inner_tol;          /* REFINE inner target (0: 1e-3)                      */
+    int64_t max_inner_sweeps;  /* REFINE inner sweeps per outer step at most (0: 60) */
+} asyrk_server_opts;
+
+typedef struct asyrk_server_stats {
+    int64_t submitted, completed, queued, active;
+    int64_t iterations;        /* engine steps run                                   */
+    int64_t kernel_launches;   /* kernels the engine launched                        */
+    int64_t mem_used;          /* bytes charged against the budget now               */
+    int64_t mem_budget;
+    int64_t arena_reserved;    /* bytes the arena holds from cudaMalloc              */
+    int32_t max_slots;
+    int32_t max_active;        /* most requests in flight at once so far             */
+    int32_t fatal;             /* first hard error of the engine, or OK              */
+    int32_t reserved;
+} asyrk_server_stats;
+
+/* Start a server on the current device.  Errors: EINVAL, ENOMEM, ECUDA. */
+int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *opts);
+
+/* Queue a request; x0 (n doubles, NULL = zeros) and x_true (n doubles, NULL =
+ * measure ||b - Ax||/||b||) are host arrays copied before the call returns.
+ * The tolerance applies to ||x-x*||/||x*|| with x_true, else to the residual.
+ * Errors: EINVAL (FP64 problem, mode not ASYNC/REFINE, gamma outside (0, 2),
+ * tol <= 0, max_sweeps < 1, server stopping), ENOMEM (needs more than the whole
+ * budget; nothing is queued). */
+int asyrk_server_submit(asyrk_server *s, asyrk_problem *p, const double *x0,
+                        const double *x_true, double gamma, double tol, int mode,
+                        int64_t max_sweeps, uint64_t *ticket);
+
+/* Wait up to timeout_us microseconds (< 0: no limit) for a request; on
+ * completion copy its x (n doubles, may be NULL) and info (info.seconds = time
+ * from submit to completion) and forget the ticket.  Returns the request's
+ * status (OK, NOT_CONVERGED, DIVERGED, ECANCELED, or the engine's hard error),
+ * ETIMEOUT (the ticket stays valid), or EINVAL (unknown ticket). */
+int asyrk_server_wait(asyrk_server *s, uint64_t ticket, double *x, asyrk_solve_info *info,
+                      int64_t timeout_us);
+
+/* Cancel a request: a queued one completes at once, a running one at the
+ * end of the current engine step, with status ECANCELED.  Errors: EINVAL. */
+int asyrk_server_cancel(asyrk_server *s, uint64_t ticket);
+
+int asyrk_server_get_stats(asyrk_server *s, asyrk_server_stats *stats);
+
+/* Stop the engine; unfinished requests complete with ECANCELED and every
+ * ticket is forgotten. */
+void asyrk_server_destroy(asyrk_server *s);
 
 /* Largest m accepted by asyrk_residual_noalloc. */
 #define ASYRK_NOALLOC_MAX_ROWS 16777216

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libasyrk.so")
 
 F64, F32, BF16 = 0, 1, 2
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_CONVERGED, DIVERGED = 0, -1, -2, -3, -4, 1, 2
+ECANCELED = -5
 MODE_SEQUENTIAL, MODE_ASYNC, MODE_REFINE = 0, 1, 2
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
 
@@ -71,7 +72,9 @@ EXPORTS = ["asyrk_create", "asyrk_destroy", "asyrk_solve", "asyrk_residual", "as
            "asyrk_get_position", "asyrk_set_position", "asyrk_problem_get_stats",
            "asyrk_strerror", "asyrk_last_error", "asyrk_abi_version", "asyrk_probe",
            "asyrk_residual_noalloc", "asyrk_autotune", "asyrk_batch_create", "asyrk_batch_solve",
-           "asyrk_batch_destroy"]
+           "asyrk_batch_destroy", "asyrk_server_create", "asyrk_server_submit",
+           "asyrk_server_wait", "asyrk_server_cancel", "asyrk_server_get_stats",
+           "asyrk_server_destroy"]
 NOALLOC_MAX_ROWS = 16777216
 PROBE_RED_F32, PROBE_GATHER_F32, PROBE_GATHER_RED, PROBE_STREAM = 0, 1, 2, 3
 
@@ -126,6 +129,19 @@ def load(path: str = LIB_PATH):
     lib.asyrk_batch_solve.restype = ctypes.c_int
     lib.asyrk_batch_destroy.argtypes = [P]
     lib.asyrk_batch_destroy.restype = None
+    lib.asyrk_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ServerOpts)]
+    lib.asyrk_server_create.restype = ctypes.c_int
+    lib.asyrk_server_submit.argtypes = [P, P, P, P, f64, f64, ctypes.c_int, i64,
+                                        ctypes.POINTER(u64)]
+    lib.asyrk_server_submit.restype = ctypes.c_int
+    lib.asyrk_server_wait.argtypes = [P, u64, P, ctypes.POINTER(SolveInfo), i64]
+    lib.asyrk_server_wait.restype = ctypes.c_int
+    lib.asyrk_server_cancel.argtypes = [P, u64]
+    lib.asyrk_server_cancel.restype = ctypes.c_int
+    lib.asyrk_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    lib.asyrk_server_get_stats.restype = ctypes.c_int
+    lib.asyrk_server_destroy.argtypes = [P]
+    lib.asyrk_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -150,6 +166,25 @@ class BatchInfo(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("device_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("resident_warps", ctypes.c_int32),
                 ("graph", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
+                ("row_exclusion", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("max_inner_sweeps", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("iterations", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("mem_used", ctypes.c_int64), ("mem_budget", ctypes.c_int64),
+                ("arena_reserved", ctypes.c_int64), ("max_slots", ctypes.c_int32),
+                ("max_active", ctypes.c_int32), ("fatal", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -284,6 +319,48 @@ def asyrk_batch_destroy(b):
     load().asyrk_batch_destroy(b)
 
 
+def asyrk_server_create(mem_budget_bytes, max_slots=0, row_exclusion=0, inner_tol=0.0,
+                        max_inner_sweeps=0):
+    h = ctypes.c_void_p()
+    o = ServerOpts(mem_budget_bytes=int(mem_budget_bytes), max_slots=max_slots,
+                   row_exclusion=row_exclusion, inner_tol=inner_tol,
+                   max_inner_sweeps=max_inner_sweeps)
+    st = load().asyrk_server_create(ctypes.byref(h), ctypes.byref(o))
+    return st, h
+
+
+def asyrk_server_submit(sv, problem_h, x0=None, x_true=None, gamma=1.0, tol=1e-6,
+                        mode=MODE_ASYNC, max_sweeps=1000):
+    t = ctypes.c_uint64()
+    x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+    xt = None if x_true is None else np.ascontiguousarray(x_true, dtype=np.float64)
+    st = load().asyrk_server_submit(sv, problem_h, _ptr(x0), _ptr(xt), float(gamma), float(tol),
+                                    mode, int(max_sweeps), ctypes.byref(t))
+    return st, t.value
+
+
+def asyrk_server_wait(sv, ticket, n, timeout_us=-1):
+    """Returns (status, x (n doubles) or None on timeout, SolveInfo)."""
+    x = np.zeros(n)
+    info = SolveInfo()
+    st = load().asyrk_server_wait(sv, ticket, _ptr(x), ctypes.byref(info), int(timeout_us))
+    return st, (None if st == ETIMEOUT else x), info
+
+
+def asyrk_server_cancel(sv, ticket):
+    return load().asyrk_server_cancel(sv, ticket)
+
+
+def asyrk_server_get_stats(sv):
+    s = ServerStats()
+    st = load().asyrk_server_get_stats(sv, ctypes.byref(s))
+    return st, s
+
+
+def asyrk_server_destroy(sv):
+    load().asyrk_server_destroy(sv)
+
+
 def asyrk_get_position(h):
     j = ctypes.c_uint64()
     st = load().asyrk_get_position(h, ctypes.byref(j))
@@ -410,6 +487,51 @@ class Batch:
         if self.b is not None and self.b.value:
             asyrk_batch_destroy(self.b)
         self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Owns one asyrk_server (continuous batching of solve requests)."""
+
+    def __init__(self, mem_budget_bytes, max_slots=0, row_exclusion=0, inner_tol=0.0,
+                 max_inner_sweeps=0):
+        st, h = asyrk_server_create(mem_budget_bytes, max_slots, row_exclusion, inner_tol,
+                                    max_inner_sweeps)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_server_create")
+        self.h = h
+
+    def submit(self, problem, x0=None, x_true=None, gamma=1.0, tol=1e-6, mode=MODE_ASYNC,
+               max_sweeps=1000):
+        st, t = asyrk_server_submit(self.h, problem.h, x0, x_true, gamma, tol, mode, max_sweeps)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_server_submit")
+        return t
+
+    def wait(self, ticket, n, timeout_us=-1):
+        return asyrk_server_wait(self.h, ticket, n, timeout_us)
+
+    def cancel(self, ticket):
+        return asyrk_server_cancel(self.h, ticket)
+
+    def stats(self):
+        return asyrk_server_get_stats(self.h)[1].as_dict()
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            asyrk_server_destroy(self.h)
+        self.h = None
 
     def __del__(self):
         try:

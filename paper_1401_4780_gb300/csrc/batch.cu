@@ -45,11 +45,6 @@ struct asyrk_batch {
     int64_t launches_per_iter = 4;
 };
 
-namespace asyrk {
-int choose_subwarp(int64_t max_len, int64_t nnz, int64_t m);
-int tuned_subwarp(int dtype, int64_t max_len, int64_t nnz, int64_t m, bool *found);
-}
-
 using namespace asyrk;
 
 static void batch_free(asyrk_batch *b)

@@ -56,7 +56,20 @@ struct SysDesc {
     int chunk0, nchunks;  // check blocks of this slot
     unsigned chk_count;   // last-block counter of the check
     unsigned res_count;   // last-block counter of the final residual
+    // mixed-precision refinement (mode 1): x is the FP32 correction d, x64 the
+    // FP64 iterate, r32 the FP32 right-hand side r = b - A x64 of the inner solve
+    int mode;             // 0: plain FP32 solve, 1: FP64 refinement
+    int phase;            // 0: projections; 1: outer step pending
+    float *r32;
+    double inner_tol;     // inner solve: ||r - A d|| / ||r|| target
+    long long inner_sweeps, max_inner;
+    int outer_steps;
+    unsigned out_count;   // last-block counter of the outer step
+    double outer_ref;     // ||x*|| (with x*) or ||b|| for the outer measure
 };
+
+constexpr int SLOT_PLAIN = 0;
+constexpr int SLOT_REFINE = 1;
 
 // warps of the project kernel that are resident on the whole GPU at once
 int batch_resident_warps(int sm_count, bool excl, int *warps);
@@ -74,6 +87,15 @@ int launch_batch_measure(SysDesc *d, int count, int total_chunks, double *part, 
 // Final FP64 residual of every slot from its x64 staging (res2, bb2).
 int launch_batch_residual(SysDesc *d, int count, int total_chunks, double *part, cudaStream_t s);
 
+// plan, project, check and (with_outer) the outer step of refinement slots
+// whose phase is 1: x64 += d, d = 0, then r = b - A x64 in FP64 (stored to
+// r32), the outer measure and the decision.  Returns without a cond kernel.
+int launch_engine_step(SysDesc *d, int count, int total_chunks, double *part, int resident_warps,
+                       bool excl, bool with_outer, cudaStream_t s);
+int launch_batch_outer(SysDesc *d, int count, int total_chunks, double *part, cudaStream_t s);
+
+int choose_subwarp(int64_t max_len, int64_t nnz, int64_t m);
+int tuned_subwarp(int dtype, int64_t max_len, int64_t nnz, int64_t m, bool *found);
 // x64 <-> x conversions over all slots (n_total entries laid out slot by slot)
 int launch_batch_convert(const double *x64, float *x, int64_t n_total, bool to_f32, cudaStream_t s);
 

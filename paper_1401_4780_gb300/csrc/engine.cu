@@ -25,11 +25,11 @@ __global__ void k_batch_plan(SysDesc *d, int count, int R)
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double wtot = 0.0;
     for (int s = 0; s < count; ++s)
-        if (d[s].active) wtot += d[s].work;
+        if (d[s].active && d[s].phase == 0) wtot += d[s].work;
     int used = 0;
     for (int s = 0; s < count; ++s) {
         int w = 0;
-        if (d[s].active && wtot > 0.0) {
+        if (d[s].active && d[s].phase == 0 && wtot > 0.0) {
             w = (int)((double)R * d[s].work / wtot);
             if (w < 1) w = 1;
             if (w > d[s].cap_warps) w = d[s].cap_warps;
@@ -41,11 +41,11 @@ __global__ void k_batch_plan(SysDesc *d, int count, int R)
     for (int pass = 0; pass < 2 && used < R; ++pass) {
         double wunc = 0.0;
         for (int s = 0; s < count; ++s)
-            if (d[s].active && d[s].nwarps < d[s].cap_warps) wunc += d[s].work;
+            if (d[s].active && d[s].phase == 0 && d[s].nwarps < d[s].cap_warps) wunc += d[s].work;
         if (wunc <= 0.0) break;
         const int left = R - used;
         for (int s = 0; s < count && used < R; ++s) {
-            if (!d[s].active || d[s].nwarps >= d[s].cap_warps) continue;
+            if (!d[s].active || d[s].phase != 0 || d[s].nwarps >= d[s].cap_warps) continue;
             int add = (int)((double)left * d[s].work / wunc);
             if (add > d[s].cap_warps - d[s].nwarps) add = d[s].cap_warps - d[s].nwarps;
             if (add > R - used) add = R - used;
@@ -58,7 +58,7 @@ __global__ void k_batch_plan(SysDesc *d, int count, int R)
         if (acc + d[s].nwarps > R) d[s].nwarps = R - acc > 0 ? R - acc : 0;
         d[s].warp0 = acc;
         acc += d[s].nwarps;
-        if (d[s].first_nwarps == 0) d[s].first_nwarps = d[s].nwarps;
+        if (d[s].first_nwarps == 0) d[s].first_nwarps = d[s].nwarps;  // reported workers
     }
 }
 
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_batch_project(SysDesc *d, int count)
     const int s = find_slot_warp(d, count, gw);
     if (s < 0) return;
     const SysDesc &D = d[s];
-    if (!D.active || gw >= D.warp0 + D.nwarps) return;  // warp-uniform
+    if (!D.active || D.phase != 0 || gw >= D.warp0 + D.nwarps) return;  // warp-uniform
     ProjArgs a;
     a.rec = D.rec;
     a.col = D.col;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) k_batch_check(SysDesc *d, int count, doub
     if (!D.active || (!measure_only && D.nwarps == 0)) return;  // same for all blocks of s
     const int k = c - D.chunk0;
     double v0 = 0.0, v1 = 0.0;
-    if (D.xt) {
+    if (D.xt && D.mode == SLOT_PLAIN) {
         const long long lo = (long long)k * BATCH_ERR_CHUNK;
         long long hi = lo + BATCH_ERR_CHUNK;
         if (hi > D.n) hi = D.n;
@@ -271,6 +271,18 @@ __global__ void __launch_bounds__(256) k_batch_check(SysDesc *d, int count, doub
     }
     D.j += D.m;
     D.sweeps += 1;
+    if (D.meas0 < 0.0) D.meas0 = meas;  // slots started without a first measure
+    if (D.mode == SLOT_REFINE) {  // inner solve of A d = r: hand over to the outer step
+        D.inner_sweeps += 1;
+        if (!isfinite(meas)) {
+            D.active = 0;
+            D.status = ASYRK_DIVERGED;
+        } else if (meas <= D.inner_tol || D.inner_sweeps >= D.max_inner ||
+                   D.sweeps >= D.max_sweeps) {
+            D.phase = 1;
+        }
+        return;
+    }
     if (!isfinite(meas) || meas > 1e30 * (D.meas0 > 0.0 ? D.meas0 : 1.0)) {
         D.active = 0;
         D.status = ASYRK_DIVERGED;
@@ -309,6 +321,81 @@ __global__ void __launch_bounds__(256) k_batch_residual(SysDesc *d, int count, d
     if (!slot_reduce(v0, v1, part, c, D.chunk0, D.nchunks, &D.res_count, t0, t1)) return;
     D.res2 = t0;
     D.bb2 = t1;
+}
+
+// outer step, part 1: x64 += d and d = 0 over the slot's x entries
+__global__ void __launch_bounds__(256) k_batch_outer_update(SysDesc *d, int count)
+{
+    const int c = blockIdx.x;
+    const int s = find_slot_chunk(d, count, c);
+    if (s < 0) return;
+    SysDesc &D = d[s];
+    if (c >= D.chunk0 + D.nchunks || !D.active || D.mode != SLOT_REFINE || D.phase != 1) return;
+    const long long lo = (long long)(c - D.chunk0) * BATCH_ERR_CHUNK;
+    long long hi = lo + BATCH_ERR_CHUNK;
+    if (hi > D.n) hi = D.n;
+    for (long long t = lo + threadIdx.x; t < hi; t += 256) {
+        D.x64[t] += (double)D.x[t];
+        D.x[t] = 0.f;
+    }
+}
+
+// outer step, part 2: r = b - A x64 (FP64) into r32, ||r||, ||x64 - x*||, decision
+__global__ void __launch_bounds__(256) k_batch_outer_residual(SysDesc *d, int count, double *part)
+{
+    const int c = blockIdx.x;
+    const int s = find_slot_chunk(d, count, c);
+    if (s < 0) return;
+    SysDesc &D = d[s];
+    if (c >= D.chunk0 + D.nchunks || !D.active || D.mode != SLOT_REFINE || D.phase != 1) return;
+    const int k = c - D.chunk0;
+    double v0 = 0.0, v1 = 0.0;
+    {
+        const long long lo = (long long)k * BATCH_ROW_CHUNK;
+        long long hi = lo + BATCH_ROW_CHUNK;
+        if (hi > D.m) hi = D.m;
+        for (long long i = lo + threadIdx.x; i < hi; i += 256) {
+            const RowRec r = D.rec[i];
+            double acc = 0.0;
+            for (unsigned q = 0; q < r.len; ++q)
+                acc += slot_value(D.dtype, D.val, r.start + q) * D.x64[D.col[r.start + q]];
+            const double ri = D.b64[i] - acc;
+            D.r32[i] = (float)ri;
+            v0 += ri * ri;
+        }
+    }
+    if (D.xt) {
+        const long long lo = (long long)k * BATCH_ERR_CHUNK;
+        long long hi = lo + BATCH_ERR_CHUNK;
+        if (hi > D.n) hi = D.n;
+        for (long long t = lo + threadIdx.x; t < hi; t += 256) {
+            const double e = D.x64[t] - D.xt[t];
+            v1 += e * e;
+        }
+    }
+    double t0, t1;
+    if (!slot_reduce(v0, v1, part, c, D.chunk0, D.nchunks, &D.out_count, t0, t1)) return;
+    const double rnorm = sqrt(t0);
+    // outer measure: ||x64 - x*|| / ||x*|| with x*, else ||b - A x64|| / ||b||
+    const double meas = D.xt ? sqrt(t1) / D.outer_ref : rnorm / D.outer_ref;
+    D.meas = meas;
+    if (D.meas0 < 0.0) D.meas0 = meas;
+    D.outer_steps += 1;
+    D.res2 = t0;
+    if (!isfinite(meas) || meas > 1e30 * (D.meas0 > 0.0 ? D.meas0 : 1.0)) {
+        D.active = 0;
+        D.status = ASYRK_DIVERGED;
+    } else if (meas <= D.tol || rnorm == 0.0) {
+        D.active = 0;
+        D.status = ASYRK_OK;
+    } else if (D.sweeps >= D.max_sweeps) {
+        D.active = 0;
+        D.status = ASYRK_NOT_CONVERGED;
+    } else {
+        D.phase = 0;  // next inner solve of A d = r
+        D.ref = rnorm;
+        D.inner_sweeps = 0;
+    }
 }
 
 // d_iter[0]: iterations done, d_iter[1]: the iteration bound
@@ -356,9 +443,8 @@ int batch_resident_warps(int sm_count, bool excl, int *warps)
     return ASYRK_OK;
 }
 
-int launch_batch_iteration(SysDesc *d, int count, int total_chunks, double *part,
-                           int resident_warps, bool excl, int *d_active, int *d_iter,
-                           bool use_cond, unsigned long long cond_handle, cudaStream_t s)
+int launch_engine_step(SysDesc *d, int count, int total_chunks, double *part, int resident_warps,
+                       bool excl, bool with_outer, cudaStream_t s)
 {
     k_batch_plan<<<1, 32, 0, s>>>(d, count, resident_warps);
     ASYRK_CK(cudaGetLastError());
@@ -368,10 +454,36 @@ int launch_batch_iteration(SysDesc *d, int count, int total_chunks, double *part
     else
         k_batch_project<false><<<blocks, 256, 0, s>>>(d, count);
     ASYRK_CK(cudaGetLastError());
-    k_batch_check<<<(unsigned)total_chunks, 256, 0, s>>>(d, count, part, 0);
-    ASYRK_CK(cudaGetLastError());
+    if (total_chunks > 0) {
+        k_batch_check<<<(unsigned)total_chunks, 256, 0, s>>>(d, count, part, 0);
+        ASYRK_CK(cudaGetLastError());
+        if (with_outer) {
+            k_batch_outer_update<<<(unsigned)total_chunks, 256, 0, s>>>(d, count);
+            ASYRK_CK(cudaGetLastError());
+            k_batch_outer_residual<<<(unsigned)total_chunks, 256, 0, s>>>(d, count, part);
+            ASYRK_CK(cudaGetLastError());
+        }
+    }
+    return ASYRK_OK;
+}
+
+int launch_batch_iteration(SysDesc *d, int count, int total_chunks, double *part,
+                           int resident_warps, bool excl, int *d_active, int *d_iter,
+                           bool use_cond, unsigned long long cond_handle, cudaStream_t s)
+{
+    int st = launch_engine_step(d, count, total_chunks, part, resident_warps, excl, false, s);
+    if (st != ASYRK_OK) return st;
     k_batch_cond<<<1, 256, 0, s>>>(d, count, d_active, d_iter, use_cond ? 1 : 0,
                                    (cudaGraphConditionalHandle)cond_handle);
+    ASYRK_CK(cudaGetLastError());
+    return ASYRK_OK;
+}
+
+int launch_batch_outer(SysDesc *d, int count, int total_chunks, double *part, cudaStream_t s)
+{
+    k_batch_outer_update<<<(unsigned)total_chunks, 256, 0, s>>>(d, count);
+    ASYRK_CK(cudaGetLastError());
+    k_batch_outer_residual<<<(unsigned)total_chunks, 256, 0, s>>>(d, count, part);
     ASYRK_CK(cudaGetLastError());
     return ASYRK_OK;
 }

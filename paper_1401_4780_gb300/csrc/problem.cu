@@ -484,6 +484,7 @@ extern "C" const char *asyrk_strerror(int status)
     case ASYRK_ENOMEM: return "out of memory";
     case ASYRK_ECUDA: return "CUDA error";
     case ASYRK_ETIMEOUT: return "timed out";
+    case ASYRK_ECANCELED: return "cancelled";
     case ASYRK_NOT_CONVERGED: return "tolerance not reached within max_sweeps";
     case ASYRK_DIVERGED: return "iteration diverged";
     default: return "unknown status";

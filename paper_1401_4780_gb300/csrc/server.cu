@@ -1,0 +1,639 @@
+// server.cu -- asyrk_server_*: continuous batching of solve requests.
+//
+// Requests name a problem that is already resident (asyrk_create) and bring
+// their own x0 (and optionally x*), step length, tolerance and mode.  An engine
+// thread owns the GPU side and repeats:
+//   admit    queued requests enter free slots while the device-memory budget
+//            allows (a slot's iterate, staging, claim bits and refinement
+//            residual come from a native arena; a problem's own bytes count
+//            once while any request uses it);
+//   iterate  one engine step over all occupied slots (batch.cuh: plan,
+//            project, check, and the outer step of refinement slots), so the
+//            row projections of every admitted request share one persistent
+//            kernel launch;
+//   harvest  finished slots copy their x back, free their memory and wake
+//            the request's waiter; the next admission can take the slot.
+// Every slot has its own Philox stream (the ticket), so one problem can serve
+// several requests at once.  The device never waits on the host: every wait
+// is host-side and has a time limit.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "batch.cuh"
+
+namespace asyrk {
+
+// ---------------------------------------------------------------------------
+// Device arena: chunks from cudaMalloc, carved first-fit into 256-byte aligned
+// blocks; a freed block coalesces with free neighbours.
+// ---------------------------------------------------------------------------
+class Arena {
+  public:
+    explicit Arena(size_t limit) : limit_(limit) {}
+    ~Arena()
+    {
+        for (auto &c : chunks_) cudaFree(c.base);
+    }
+    Arena(const Arena &) = delete;
+    Arena &operator=(const Arena &) = delete;
+
+    // nullptr when the limit would be exceeded or cudaMalloc fails
+    void *alloc(size_t bytes)
+    {
+        bytes = round(bytes);
+        for (auto &c : chunks_) {
+            for (auto it = c.free.begin(); it != c.free.end(); ++it) {
+                if (it->second < bytes) continue;
+                const size_t off = it->first, len = it->second;
+                c.free.erase(it);
+                if (len > bytes) c.free[off + bytes] = len - bytes;
+                return c.base + off;
+            }
+        }
+        size_t sz = bytes > kChunk ? bytes : kChunk;
+        if (reserved_ + sz > limit_) sz = bytes;
+        if (reserved_ + sz > limit_) return nullptr;
+        Chunk c;
+        if (cudaMalloc((void **)&c.base, sz) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        c.size = sz;
+        if (sz > bytes) c.free[bytes] = sz - bytes;
+        reserved_ += sz;
+        chunks_.push_back(std::move(c));
+        return chunks_.back().base;
+    }
+
+    void release(void *p, size_t bytes)
+    {
+        if (!p) return;
+        bytes = round(bytes);
+        char *q = static_cast<char *>(p);
+        for (auto &c : chunks_) {
+            if (q < c.base || q >= c.base + c.size) continue;
+            size_t off = (size_t)(q - c.base), len = bytes;
+            auto next = c.free.lower_bound(off);
+            if (next != c.free.end() && off + len == next->first) {
+                len += next->second;
+                next = c.free.erase(next);
+            }
+            if (next != c.free.begin()) {
+                auto prev = std::prev(next);
+                if (prev->first + prev->second == off) {
+                    off = prev->first;
+                    len += prev->second;
+                    c.free.erase(prev);
+                }
+            }
+            c.free[off] = len;
+            return;
+        }
+    }
+
+    size_t reserved() const { return reserved_; }
+
+  private:
+    static constexpr size_t kChunk = (size_t)256 << 20;
+    static size_t round(size_t b) { return (b + 255) & ~(size_t)255; }
+    struct Chunk {
+        char *base = nullptr;
+        size_t size = 0;
+        std::map<size_t, size_t> free;  // offset -> length
+    };
+    std::vector<Chunk> chunks_;
+    size_t limit_;
+    size_t reserved_ = 0;
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    asyrk_problem *p = nullptr;
+    std::vector<double> x0, xt, result;
+    double gamma = 1.0, tol = 0.0;
+    int mode = ASYRK_MODE_ASYNC;
+    int64_t max_sweeps = 0;
+    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    int status = ASYRK_NOT_CONVERGED;
+    bool done = false, cancelled = false;
+    int slot = -1;
+    size_t slot_bytes = 0;
+    asyrk_solve_info info;
+};
+
+struct SlotMem {
+    float *x = nullptr;
+    double *x64 = nullptr, *xt = nullptr;
+    unsigned *busy = nullptr;
+    float *r32 = nullptr;
+    size_t bx = 0, bx64 = 0, bxt = 0, bbusy = 0, br32 = 0;
+};
+
+static double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+}  // namespace asyrk
+
+using namespace asyrk;
+
+struct asyrk_server {
+    int max_slots = 0;
+    size_t budget = 0;
+    bool excl = true;
+    int device = 0;
+    int resident_warps = 0;
+    double inner_tol = 1e-3;
+    int64_t max_inner = 60;
+    cudaStream_t s = nullptr;
+    SysDesc *d = nullptr;
+    std::vector<SysDesc> h;
+    std::vector<Request *> slot_req;
+    std::vector<SlotMem> slot_mem;
+    double *part = nullptr;
+    int part_cap = 0;
+    Arena *arena = nullptr;
+    size_t used = 0;
+    std::map<asyrk_problem *, int> problem_refs;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, Request *> reqs;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    int fatal = ASYRK_OK;
+    std::thread th;
+
+    int64_t submitted = 0, completed = 0, iterations = 0, launches = 0, max_active = 0;
+};
+
+static size_t request_bytes(const asyrk_problem *p, bool has_xt, int mode)
+{
+    size_t b = (size_t)p->n * (4 + 8) + (size_t)((p->m + 31) / 32) * 4;
+    if (has_xt) b += (size_t)p->n * 8;
+    if (mode == ASYRK_MODE_REFINE) b += (size_t)p->m * 4;
+    return b + 5 * 256;
+}
+
+static void free_slot_mem(asyrk_server *sv, int k)
+{
+    SlotMem &M = sv->slot_mem[k];
+    sv->arena->release(M.x, M.bx);
+    sv->arena->release(M.x64, M.bx64);
+    sv->arena->release(M.xt, M.bxt);
+    sv->arena->release(M.busy, M.bbusy);
+    sv->arena->release(M.r32, M.br32);
+    M = SlotMem();
+}
+
+// complete a request, with sv->mu held
+static void finish_locked(asyrk_server *sv, Request *r, int status)
+{
+    r->status = status;
+    r->info.status = status;
+    r->t_done = now_s();
+    r->info.seconds = r->t_done - r->t_submit;
+    r->done = true;
+    sv->completed += 1;
+    sv->cv_done.notify_all();
+}
+
+// admit request r into slot k (engine thread, sv->mu held); false: no memory now
+static bool admit_locked(asyrk_server *sv, Request *r, int k)
+{
+    asyrk_problem *p = r->p;
+    const bool has_xt = !r->xt.empty();
+    const bool refine = r->mode == ASYRK_MODE_REFINE;
+    const size_t need = r->slot_bytes + (sv->problem_refs.count(p) ? 0 : (size_t)p->dev_bytes);
+    if (sv->used + need > sv->budget) return false;
+    SlotMem M;
+    M.bx = (size_t)p->n * 4;
+    M.bx64 = (size_t)p->n * 8;
+    M.bbusy = (size_t)((p->m + 31) / 32) * 4;
+    M.bxt = has_xt ? (size_t)p->n * 8 : 0;
+    M.br32 = refine ? (size_t)p->m * 4 : 0;
+    M.x = (float *)sv->arena->alloc(M.bx);
+    M.x64 = (double *)sv->arena->alloc(M.bx64);
+    M.busy = (unsigned *)sv->arena->alloc(M.bbusy);
+    if (has_xt) M.xt = (double *)sv->arena->alloc(M.bxt);
+    if (refine) M.r32 = (float *)sv->arena->alloc(M.br32);
+    sv->slot_mem[k] = M;
+    if (!M.x || !M.x64 || !M.busy || (has_xt && !M.xt) || (refine && !M.r32)) {
+        free_slot_mem(sv, k);
+        return false;
+    }
+    sv->used += need;
+    sv->problem_refs[p] += 1;
+    // x0 -> x64; plain slots iterate on x (FP32); refinement slots keep x64 as
+    // the iterate and x as the FP32 correction, starting at zero
+    cudaMemcpyAsync(M.x64, r->x0.data(), M.bx64, cudaMemcpyHostToDevice, sv->s);
+    if (has_xt) cudaMemcpyAsync(M.xt, r->xt.data(), M.bxt, cudaMemcpyHostToDevice, sv->s);
+    cudaMemsetAsync(M.busy, 0, M.bbusy, sv->s);
+    if (refine) {
+        cudaMemsetAsync(M.x, 0, M.bx, sv->s);
+    } else {
+        launch_batch_convert(M.x64, M.x, p->n, true, sv->s);
+        sv->launches += 1;
+    }
+    SysDesc &D = sv->h[k];
+    memset(&D, 0, sizeof D);
+    bool tuned = false;
+    int G = tuned_subwarp(p->dtype, p->max_len, p->nnz, p->m, &tuned);
+    if (!tuned) G = choose_subwarp(p->max_len, p->nnz, p->m);
+    const long long capw = tau_cap_estimate(p->m, p->n);
+    const long long cw = (capw * G + 31) / 32;
+    D.G = G;
+    D.cap_warps = (int)(cw < 1 ? 1 : cw > 0x7fffffff ? 0x7fffffff : cw);
+    D.rec = p->rec;
+    D.col = p->col;
+    D.val = p->val;
+    D.b64 = p->b64;
+    D.x = M.x;
+    D.x64 = M.x64;
+    D.xt = M.xt;
+    D.busy = M.busy;
+    D.r32 = M.r32;
+    D.bvec = refine ? M.r32 : nullptr;
+    D.m = (unsigned)p->m;
+    D.n = (unsigned)p->n;
+    D.dtype = p->dtype;
+    D.uniform = p->uniform;
+    D.work = (double)p->nnz;
+    D.key = make_uint2((unsigned)p->seed, (unsigned)(p->seed >> 32));
+    D.stream_id = (unsigned)r->ticket;  // each request draws its own row sequence
+    D.j = 0;
+    D.gamma = (float)r->gamma;
+    D.tol = r->tol;
+    D.max_sweeps = r->max_sweeps;
+    D.active = 1;
+    D.status = ASYRK_NOT_CONVERGED;
+    D.meas = -1.0;
+    D.meas0 = -1.0;
+    double xtn = 0.0;
+    for (double v : r->xt) xtn += v * v;
+    xtn = sqrt(xtn);
+    const double bn = p->bnorm > 0.0 ? p->bnorm : 1.0;
+    D.mode = refine ? SLOT_REFINE : SLOT_PLAIN;
+    D.phase = refine ? 1 : 0;  // refinement starts with an outer step: r = b - A x0
+    D.ref = has_xt ? (xtn > 0.0 ? xtn : 1.0) : bn;
+    D.outer_ref = D.ref;
+    D.inner_tol = sv->inner_tol;
+    D.max_inner = sv->max_inner;
+    sv->slot_req[k] = r;
+    r->slot = k;
+    r->t_admit = now_s();
+    return true;
+}
+
+static void release_slot_locked(asyrk_server *sv, int k)
+{
+    Request *r = sv->slot_req[k];
+    asyrk_problem *p = r->p;
+    free_slot_mem(sv, k);
+    size_t give = r->slot_bytes;
+    if (--sv->problem_refs[p] == 0) {
+        sv->problem_refs.erase(p);
+        give += (size_t)p->dev_bytes;
+    }
+    sv->used -= give;
+    sv->slot_req[k] = nullptr;
+    memset(&sv->h[k], 0, sizeof(SysDesc));
+    r->slot = -1;
+}
+
+static void fail_all_locked(asyrk_server *sv, int status)
+{
+    for (int k = 0; k < sv->max_slots; ++k) {
+        if (!sv->slot_req[k]) continue;
+        Request *r = sv->slot_req[k];
+        release_slot_locked(sv, k);
+        finish_locked(sv, r, status);
+    }
+    while (!sv->queue.empty()) {
+        Request *r = sv->queue.front();
+        sv->queue.pop_front();
+        finish_locked(sv, r, status);
+    }
+}
+
+// one engine step over the occupied slots, GPU work done without the lock
+static int engine_step(asyrk_server *sv, std::unique_lock<std::mutex> &lk, std::vector<int> &done)
+{
+    int chunks = 0;
+    for (int k = 0; k < sv->max_slots; ++k) {
+        SysDesc &D = sv->h[k];
+        D.chunk0 = chunks;
+        if (!sv->slot_req[k]) {
+            D.nchunks = 0;
+            continue;
+        }
+        const int64_t ce = ((int64_t)D.n + BATCH_ERR_CHUNK - 1) / BATCH_ERR_CHUNK;
+        const int64_t cr = ((int64_t)D.m + BATCH_ROW_CHUNK - 1) / BATCH_ROW_CHUNK;
+        D.nchunks = (int)(ce > cr ? ce : cr);
+        chunks += D.nchunks;
+        if (sv->slot_req[k]->cancelled) D.active = 0;
+    }
+    if (chunks > sv->part_cap) {
+        cudaFree(sv->part);
+        sv->part = nullptr;
+        sv->part_cap = 0;
+        ASYRK_CK(cudaMalloc((void **)&sv->part, 2 * (size_t)chunks * sizeof(double)));
+        sv->part_cap = chunks;
+    }
+    lk.unlock();
+    int st = ASYRK_OK;
+    cudaError_t e = cudaMemcpyAsync(sv->d, sv->h.data(), sv->max_slots * sizeof(SysDesc),
+                                    cudaMemcpyHostToDevice, sv->s);
+    if (e == cudaSuccess)
+        st = launch_engine_step(sv->d, sv->max_slots, chunks, sv->part, sv->resident_warps,
+                                sv->excl, true, sv->s);
+    if (e == cudaSuccess && st == ASYRK_OK)
+        e = cudaMemcpyAsync(sv->h.data(), sv->d, sv->max_slots * sizeof(SysDesc),
+                            cudaMemcpyDeviceToHost, sv->s);
+    if (e == cudaSuccess && st == ASYRK_OK) e = cudaStreamSynchronize(sv->s);
+    lk.lock();
+    if (e != cudaSuccess) return cuda_fail(e, "server step", __FILE__, __LINE__);
+    if (st != ASYRK_OK) return st;
+    sv->iterations += 1;
+    sv->launches += 5;
+    done.clear();
+    for (int k = 0; k < sv->max_slots; ++k)
+        if (sv->slot_req[k] && !sv->h[k].active) done.push_back(k);
+    return ASYRK_OK;
+}
+
+// copy finished slots' x back and complete their requests
+static int harvest(asyrk_server *sv, std::unique_lock<std::mutex> &lk, const std::vector<int> &done)
+{
+    if (done.empty()) return ASYRK_OK;
+    lk.unlock();
+    cudaError_t e = cudaSuccess;
+    for (int k : done) {
+        Request *r = sv->slot_req[k];
+        const SysDesc &D = sv->h[k];
+        r->result.resize(D.n);
+        if (D.mode == SLOT_PLAIN) {
+            if (launch_batch_convert(D.x64, D.x, D.n, false, sv->s) != ASYRK_OK) e = cudaErrorUnknown;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(r->result.data(), D.x64, (size_t)D.n * sizeof(double),
+                                cudaMemcpyDeviceToHost, sv->s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sv->s);
+    lk.lock();
+    if (e != cudaSuccess) return cuda_fail(e, "server harvest", __FILE__, __LINE__);
+    for (int k : done) {
+        Request *r = sv->slot_req[k];
+        const SysDesc &D = sv->h[k];
+        asyrk_solve_info &I = r->info;
+        memset(&I, 0, sizeof I);
+        I.workers = D.first_nwarps * (32 / (D.G > 0 ? D.G : 32));
+        I.subwarp = D.G;
+        I.refine_steps = D.outer_steps;
+        I.sweeps = D.sweeps;
+        I.projections = D.sweeps * (int64_t)D.m;
+        I.skipped = (int64_t)D.skipped;
+        I.rel_err = D.xt ? D.meas : -1.0;
+        I.rel_res = D.mode == SLOT_REFINE && r->p->bnorm > 0.0 ? sqrt(D.res2) / r->p->bnorm : -1.0;
+        I.j_end = D.j;
+        const int status = r->cancelled ? ASYRK_ECANCELED : D.status;
+        release_slot_locked(sv, k);
+        finish_locked(sv, r, status);
+    }
+    sv->launches += (int64_t)done.size();
+    return ASYRK_OK;
+}
+
+static void engine_loop(asyrk_server *sv)
+{
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    std::vector<int> done;
+    for (;;) {
+        // admission: FIFO into free slots while memory allows
+        for (int k = 0; k < sv->max_slots && !sv->queue.empty(); ++k) {
+            if (sv->slot_req[k]) continue;
+            Request *r = sv->queue.front();
+            if (r->cancelled) {
+                sv->queue.pop_front();
+                finish_locked(sv, r, ASYRK_ECANCELED);
+                --k;
+                continue;
+            }
+            if (!admit_locked(sv, r, k)) break;
+            sv->queue.pop_front();
+        }
+        int occupied = 0;
+        for (int k = 0; k < sv->max_slots; ++k) occupied += sv->slot_req[k] ? 1 : 0;
+        if (occupied > sv->max_active) sv->max_active = occupied;
+        if (sv->stop) {
+            fail_all_locked(sv, ASYRK_ECANCELED);
+            break;
+        }
+        if (occupied == 0) {
+            sv->cv_work.wait_for(lk, std::chrono::milliseconds(50),
+                                 [&] { return sv->stop || !sv->queue.empty(); });
+            continue;
+        }
+        int st = engine_step(sv, lk, done);
+        if (st == ASYRK_OK) st = harvest(sv, lk, done);
+        if (st != ASYRK_OK) {
+            sv->fatal = st;
+            fail_all_locked(sv, st);
+            sv->stop = true;
+            break;
+        }
+    }
+}
+
+extern "C" int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *opts)
+{
+    if (!out) return set_error(ASYRK_EINVAL, "out is NULL");
+    *out = nullptr;
+    asyrk_server_opts o;
+    memset(&o, 0, sizeof o);
+    if (opts) o = *opts;
+    if (o.mem_budget_bytes <= 0) return set_error(ASYRK_EINVAL, "mem_budget_bytes must be > 0");
+    if (o.max_slots < 0) return set_error(ASYRK_EINVAL, "max_slots < 0");
+    if (o.row_exclusion < -1 || o.row_exclusion > 1)
+        return set_error(ASYRK_EINVAL, "row_exclusion must be -1, 0 or 1");
+    if (o.inner_tol < 0.0 || o.max_inner_sweeps < 0) return set_error(ASYRK_EINVAL, "bad inner solve limits");
+    asyrk_server *sv = new (std::nothrow) asyrk_server();
+    if (!sv) return set_error(ASYRK_ENOMEM, "host allocation failed");
+    auto fail = [&](int st) {
+        if (sv->s) cudaStreamDestroy(sv->s);
+        cudaFree(sv->d);
+        delete sv->arena;
+        delete sv;
+        return st;
+    };
+    sv->budget = (size_t)o.mem_budget_bytes;
+    sv->excl = o.row_exclusion >= 0;
+    if (o.inner_tol > 0.0) sv->inner_tol = o.inner_tol;
+    if (o.max_inner_sweeps > 0) sv->max_inner = o.max_inner_sweeps;
+    cudaError_t e = cudaGetDevice(&sv->device);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "device query", __FILE__, __LINE__));
+    int st = batch_resident_warps(sms, sv->excl, &sv->resident_warps);
+    if (st != ASYRK_OK) return fail(st);
+    sv->max_slots = o.max_slots > 0 ? o.max_slots : 256;
+    if (sv->max_slots > sv->resident_warps) sv->max_slots = sv->resident_warps;
+    sv->h.assign(sv->max_slots, SysDesc());
+    memset(sv->h.data(), 0, sv->max_slots * sizeof(SysDesc));
+    sv->slot_req.assign(sv->max_slots, nullptr);
+    sv->slot_mem.assign(sv->max_slots, SlotMem());
+    sv->arena = new (std::nothrow) Arena(sv->budget);
+    if (!sv->arena) return fail(set_error(ASYRK_ENOMEM, "host allocation failed"));
+    e = cudaMalloc((void **)&sv->d, sv->max_slots * sizeof(SysDesc));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "server allocation", __FILE__, __LINE__));
+    try {
+        sv->th = std::thread(engine_loop, sv);
+    } catch (...) {
+        return fail(set_error(ASYRK_ENOMEM, "could not start the engine thread"));
+    }
+    *out = sv;
+    return ASYRK_OK;
+}
+
+extern "C" int asyrk_server_submit(asyrk_server *sv, asyrk_problem *p, const double *x0,
+                                   const double *x_true, double gamma, double tol, int mode,
+                                   int64_t max_sweeps, uint64_t *ticket)
+{
+    if (!sv || !p || !ticket) return set_error(ASYRK_EINVAL, "NULL argument");
+    if (p->dtype == ASYRK_F64)
+        return set_error(ASYRK_EINVAL, "served solves take FP32 or BF16 values");
+    if (mode != ASYRK_MODE_ASYNC && mode != ASYRK_MODE_REFINE)
+        return set_error(ASYRK_EINVAL, "served mode must be ASYNC or REFINE");
+    if (!(gamma > 0.0 && gamma < 2.0)) return set_error(ASYRK_EINVAL, "gamma must be in (0, 2)");
+    if (!(tol > 0.0) || max_sweeps < 1) return set_error(ASYRK_EINVAL, "need tol > 0 and max_sweeps >= 1");
+    Request *r = new (std::nothrow) Request();
+    if (!r) return set_error(ASYRK_ENOMEM, "host allocation failed");
+    r->p = p;
+    r->x0.assign(p->n, 0.0);
+    if (x0) memcpy(r->x0.data(), x0, p->n * sizeof(double));
+    if (x_true) r->xt.assign(x_true, x_true + p->n);
+    r->gamma = gamma;
+    r->tol = tol;
+    r->mode = mode;
+    r->max_sweeps = max_sweeps;
+    r->slot_bytes = request_bytes(p, x_true != nullptr, mode);
+    memset(&r->info, 0, sizeof r->info);
+    if (r->slot_bytes + (size_t)p->dev_bytes > sv->budget) {
+        delete r;
+        return set_error(ASYRK_ENOMEM, "the request needs %zu bytes, more than the whole budget",
+                         (size_t)(request_bytes(p, x_true != nullptr, mode) + p->dev_bytes));
+    }
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (sv->stop) {
+        delete r;
+        return sv->fatal != ASYRK_OK ? sv->fatal : set_error(ASYRK_EINVAL, "server is stopping");
+    }
+    r->ticket = sv->next_ticket++;
+    r->t_submit = now_s();
+    sv->queue.push_back(r);
+    sv->reqs[r->ticket] = r;
+    sv->submitted += 1;
+    *ticket = r->ticket;
+    sv->cv_work.notify_one();
+    return ASYRK_OK;
+}
+
+extern "C" int asyrk_server_wait(asyrk_server *sv, uint64_t ticket, double *x,
+                                 asyrk_solve_info *info, int64_t timeout_us)
+{
+    if (!sv) return set_error(ASYRK_EINVAL, "NULL server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return set_error(ASYRK_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    if (timeout_us < 0) {
+        sv->cv_done.wait(lk, [&] { return r->done; });
+    } else if (!sv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; })) {
+        return set_error(ASYRK_ETIMEOUT, "request %llu not finished", (unsigned long long)ticket);
+    }
+    if (x && !r->result.empty()) memcpy(x, r->result.data(), r->result.size() * sizeof(double));
+    if (info) *info = r->info;
+    const int st = r->status;
+    sv->reqs.erase(it);
+    delete r;
+    return st;
+}
+
+extern "C" int asyrk_server_cancel(asyrk_server *sv, uint64_t ticket)
+{
+    if (!sv) return set_error(ASYRK_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return set_error(ASYRK_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    if (r->done) return ASYRK_OK;
+    r->cancelled = true;
+    for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q) {
+        if (*q == r) {
+            sv->queue.erase(q);
+            finish_locked(sv, r, ASYRK_ECANCELED);
+            break;
+        }
+    }
+    sv->cv_work.notify_one();
+    return ASYRK_OK;
+}
+
+extern "C" int asyrk_server_get_stats(asyrk_server *sv, asyrk_server_stats *st)
+{
+    if (!sv || !st) return set_error(ASYRK_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    memset(st, 0, sizeof *st);
+    st->submitted = sv->submitted;
+    st->completed = sv->completed;
+    st->queued = (int64_t)sv->queue.size();
+    int64_t act = 0;
+    for (auto *r : sv->slot_req) act += r ? 1 : 0;
+    st->active = act;
+    st->iterations = sv->iterations;
+    st->kernel_launches = sv->launches;
+    st->mem_used = (int64_t)sv->used;
+    st->mem_budget = (int64_t)sv->budget;
+    st->arena_reserved = (int64_t)sv->arena->reserved();
+    st->max_slots = sv->max_slots;
+    st->max_active = (int32_t)sv->max_active;
+    st->fatal = sv->fatal;
+    return ASYRK_OK;
+}
+
+extern "C" void asyrk_server_destroy(asyrk_server *sv)
+{
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->stop = true;
+        sv->cv_work.notify_all();
+    }
+    if (sv->th.joinable()) sv->th.join();
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        fail_all_locked(sv, ASYRK_ECANCELED);
+        for (auto &kv : sv->reqs) delete kv.second;
+        sv->reqs.clear();
+    }
+    cudaStreamSynchronize(sv->s);
+    cudaStreamDestroy(sv->s);
+    cudaFree(sv->d);
+    cudaFree(sv->part);
+    delete sv->arena;
+    delete sv;
+}

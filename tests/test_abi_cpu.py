@@ -52,6 +52,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(asyrk.BatchOpts) == 16
     assert ctypes.sizeof(asyrk.BatchInfo) == 56
     assert ctypes.sizeof(asyrk.TuneResult) == 24
+    assert ctypes.sizeof(asyrk.ServerOpts) == 32
+    assert ctypes.sizeof(asyrk.ServerStats) == 88
 
 
 def test_abi_version_and_status_strings(lib):
@@ -70,6 +72,13 @@ def test_create_rejects_bad_sizes_before_touching_the_gpu(lib, m, n):
     st, h = asyrk.asyrk_create(m, n, rp, col, val, asyrk.F64, b)
     assert st == asyrk.EINVAL and not h.value
     assert "m and n" in asyrk.asyrk_last_error()
+
+
+def test_server_argument_checks_before_touching_the_gpu(lib):
+    assert asyrk.asyrk_server_create(0)[0] == asyrk.EINVAL
+    assert asyrk.asyrk_server_create(1 << 20, max_slots=-1)[0] == asyrk.EINVAL
+    assert asyrk.asyrk_server_submit(None, None)[0] == asyrk.EINVAL
+    assert asyrk.asyrk_strerror(asyrk.ECANCELED) == "cancelled"
 
 
 def test_probe_rejects_bad_arguments_before_touching_the_gpu(lib):
