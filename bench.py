@@ -66,6 +66,11 @@ def parse_args():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--scale", type=int, default=0,
                     help="shrink m and n by 2^scale (testing only; not a bench number)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain/refine, batched and served measurements")
+    ap.add_argument("--served-seconds", type=float, default=10.0,
+                    help="length of the Poisson arrival window of the served measurement")
+    ap.add_argument("--served-rate", type=float, default=2000.0, help="requests per second")
     return ap.parse_args()
 
 
@@ -282,6 +287,209 @@ def run_reference(args, dist):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the other workloads: FP64 plain, BF16 refinement, batched, served
+# ---------------------------------------------------------------------------
+def _timed_solve(p, x, reps=3, **kw):
+    best = None
+    for _ in range(reps):
+        p.position = 0
+        x[:] = 0.0
+        st, info = p.solve(x, **kw)
+        if best is None or info.seconds < best[1].seconds:
+            best = (st, info)
+    return best
+
+
+def extras_plain_refine(asyrk, synth):
+    out = {}
+    s1 = synth.plain_f64_system()
+    with asyrk.Problem.from_system(s1) as p:
+        x = np.zeros(s1.n)
+        st, i = _timed_solve(p, x, tol=1e-8, max_sweeps=400, x_true=s1.x_true)
+        out["plain_f64_async_to_1e-8"] = {"status": st, "ms": 1e3 * i.seconds, "sweeps": i.sweeps,
+                                          "rel_err": i.rel_err, "workers": i.workers}
+    s3 = synth.bf16_refine_system()
+    s3f = synth.make_system(s3.m, s3.n, 16, s3.seed, row_norms="unit", value_dtype="f32")
+    with asyrk.Problem.from_system(s3) as p:
+        x = np.zeros(s3.n)
+        for tol in (1e-8, 1e-10):
+            st, i = _timed_solve(p, x, tol=tol, max_sweeps=2000, x_true=s3.x_true,
+                                 mode=asyrk.MODE_REFINE)
+            out["bf16_refine_to_%g" % tol] = {"status": st, "ms": 1e3 * i.seconds,
+                                               "sweeps": i.sweeps, "refine_steps": i.refine_steps,
+                                               "rel_err": i.rel_err, "rel_res": i.rel_res}
+    with asyrk.Problem.from_system(s3f) as p:
+        x = np.zeros(s3f.n)
+        st, i = _timed_solve(p, x, tol=1e-6, max_sweeps=400, x_true=s3f.x_true)
+        out["plain_fp32_kernel_to_1e-6"] = {"status": st, "ms": 1e3 * i.seconds,
+                                            "sweeps": i.sweeps, "rel_err": i.rel_err}
+        st, i = _timed_solve(p, x, reps=1, tol=1e-8, max_sweeps=300, x_true=s3f.x_true)
+        out["plain_fp32_kernel_to_1e-8"] = {"status": st, "reached_rel_err": i.rel_err,
+                                            "sweeps": i.sweeps,
+                                            "note": "FP32 iterate floor; 1e-8 needs refinement"}
+    out["workload"] = ("plain FP64: m=4096, n=1024, 16 nnz/row, unit rows; refine: same shape, "
+                       "BF16 values, FP32 inner, FP64 outer")
+    return out
+
+
+def extras_batched(asyrk, synth, torch):
+    shapes = synth.batch_shapes()
+    base = synth.config_seed(4) * 1000
+    probs, x_trues = [], []
+    for k, (m, n, L) in enumerate(shapes):
+        d = synth.make_system_torch(m, n, L, base + k, row_norms="unit", value_dtype="f32")
+        torch.cuda.synchronize()
+        probs.append(asyrk.Problem(m, n, d["row_ptr"], d["col"], d["val_store"], asyrk.F32, d["b"],
+                                   seed=synth.solver_seed(base + k), device_ptrs=True))
+        x_trues.append(d["x_true"])
+        del d
+    # the autotuner, once per row-length class (the largest system of each)
+    tuned = {}
+    by_class = {}
+    for p, (m, n, L) in zip(probs, shapes):
+        c = 1 << (L - 1).bit_length()
+        if c not in by_class or m > by_class[c][1]:
+            by_class[c] = (p, m)
+    for c, (p, _) in sorted(by_class.items()):
+        r = p.autotune()
+        tuned[str(c)] = {"subwarp": r.subwarp, "workers_at_that_m": r.workers,
+                         "projections_per_s": r.projections_per_s, "trials": r.trials}
+    xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for (_, n, _) in shapes]
+    tols = [1e-6] * len(shapes)
+    with asyrk.Batch(probs) as b:
+        b.solve(xs, tols=tols, max_sweeps=400, x_trues=x_trues, device_ptrs=True)  # warm-up
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        st, infos, bi = b.solve(xs, tols=tols, max_sweeps=400, x_trues=x_trues, device_ptrs=True)
+    errs = [float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)) for x, xt in zip(xs, x_trues)]
+    # the plain single-system FP32 kernel, one system after another, same tolerance
+    t_plain, proj_plain, ok_plain = 0.0, 0, 0
+    for p, x, xt in zip(probs, xs, x_trues):
+        x.zero_()
+        stp, ip = p.solve(x, tol=1e-6, max_sweeps=400, x_true=xt, device_ptrs=True)
+        t_plain += ip.seconds
+        proj_plain += ip.projections - ip.skipped
+        ok_plain += stp == asyrk.OK
+    sweeps = [i.sweeps for i in infos]
+    out = {"workload": "256 systems: m = floor(2^U(11,18)), n = m/4, nnz/row U{8..64} per system, "
+                       "N(0,1) values, unit rows, FP32; each to ||x-x*||/||x*|| <= 1e-6",
+           "systems": len(shapes), "sum_m": int(sum(m for m, _, _ in shapes)),
+           "sum_nnz": int(sum(m * L for m, _, L in shapes)), "status": st,
+           "converged": bi.converged, "iterations": bi.iterations, "graph_launch": bool(bi.graph),
+           "device_ms": bi.device_ms, "wall_ms": 1e3 * bi.seconds,
+           "projections_per_s": bi.projections / (bi.device_ms / 1e3),
+           "max_rel_err_host": max(errs), "sweeps_median": float(np.median(sweeps)),
+           "sweeps_max": int(max(sweeps)), "kernel_launches": bi.kernel_launches,
+           "resident_warps": bi.resident_warps, "autotuned_by_row_length_class": tuned,
+           "plain_fp32_one_at_a_time": {"wall_ms": 1e3 * t_plain, "converged": ok_plain,
+                                        "projections_per_s": proj_plain / t_plain},
+           "speedup_vs_one_at_a_time": t_plain / bi.seconds}
+    for p in probs:
+        p.close()
+    return out
+
+
+def extras_served(asyrk, synth, torch, seconds, rate):
+    import threading
+    pool = {"small_bf16": [], "small_f32": [], "large_bf16": [], "large_f32": []}
+    xts = {}
+    seed0 = synth.config_seed(5) * 1000
+    k = 0
+    for cls, (m, n, L, dt, count) in {"small_bf16": (4096, 1024, 16, "bf16", 32),
+                                      "small_f32": (4096, 1024, 16, "f32", 32),
+                                      "large_bf16": (1 << 20, 1 << 18, 32, "bf16", 2),
+                                      "large_f32": (1 << 20, 1 << 18, 32, "f32", 2)}.items():
+        for _ in range(count):
+            d = synth.make_system_torch(m, n, L, seed0 + k, row_norms="unit", value_dtype=dt)
+            torch.cuda.synchronize()
+            vd = asyrk.BF16 if dt == "bf16" else asyrk.F32
+            p = asyrk.Problem(m, n, d["row_ptr"], d["col"], d["val_store"], vd, d["b"],
+                              seed=synth.solver_seed(seed0 + k), device_ptrs=True)
+            pool[cls].append(p)
+            xts[id(p)] = d["x_true"].cpu().numpy()
+            del d
+            k += 1
+    rng = np.random.default_rng(synth.config_seed(5))
+    t, reqs = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        large = rng.random() < 0.05
+        bf16 = rng.random() < 0.5
+        tol = 1e-6 if rng.random() < 0.5 else 1e-10
+        refine = bf16 or tol < 1e-8  # 1e-10 needs FP64 refinement
+        cls = ("large_" if large else "small_") + ("bf16" if refine else "f32")
+        p = pool[cls][int(rng.integers(len(pool[cls])))]
+        reqs.append((t, p, tol, asyrk.MODE_REFINE if refine else asyrk.MODE_ASYNC, cls))
+    tickets = [None] * len(reqs)
+    sv = asyrk.Server(120 << 30, max_slots=512)
+    # warm-up: one request of each class
+    for cls in pool:
+        p = pool[cls][0]
+        tt = sv.submit(p, x_true=xts[id(p)], tol=1e-6,
+                       mode=asyrk.MODE_REFINE if cls.endswith("bf16") else asyrk.MODE_ASYNC)
+        sv.wait(tt, p.n)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for q, (ta, p, tol, mode, _) in enumerate(reqs):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[q] = sv.submit(p, x_true=xts[id(p)], tol=tol, mode=mode, max_sweeps=3000)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, ok, errs_ok = {}, 0, True
+    for q, (ta, p, tol, mode, cls) in enumerate(reqs):
+        while tickets[q] is None:
+            time.sleep(0.0005)
+        st, x, info = sv.wait(tickets[q], p.n)
+        ok += st == asyrk.OK
+        lat.setdefault(cls, []).append(info.seconds)
+        if st == asyrk.OK and not (info.rel_err <= tol * 1.0001):
+            errs_ok = False
+    t_end = time.perf_counter()
+    th.join()
+    stats = sv.stats()
+    sv.close()
+    allv = np.concatenate([np.array(v) for v in lat.values()])
+    out = {"workload": "Poisson arrivals; 95%% m=4096, n=1024, 16 nnz/row, 5%% m=2^20, n=2^18, "
+                       "32 nnz/row (unit rows); mode FP32 or BF16+FP64 refinement, tol 1e-6 or "
+                       "1e-10 (1e-10 always refined); budget 120 GB; pool of 68 resident problems",
+           "offered_rate_per_s": rate, "window_s": seconds, "requests": len(reqs),
+           "converged": ok, "all_errors_within_tol": errs_ok,
+           "solves_per_s": len(reqs) / (t_end - t0),
+           "p50_ms": 1e3 * float(np.percentile(allv, 50)),
+           "p99_ms": 1e3 * float(np.percentile(allv, 99)),
+           "per_class": {c: {"n": len(v), "p50_ms": 1e3 * float(np.percentile(v, 50)),
+                             "p99_ms": 1e3 * float(np.percentile(v, 99))}
+                         for c, v in sorted(lat.items())},
+           "engine_steps": stats["iterations"], "max_in_flight": stats["max_active"]}
+    # the plain single-system FP32 kernel, one request at a time, at 1e-6
+    times = {}
+    for cls, count in (("small_f32", 16), ("large_f32", 2)):
+        ts = []
+        for q in range(count):
+            p = pool[cls][q % len(pool[cls])]
+            x = np.zeros(p.n)
+            p.position = 0
+            stp, ip = p.solve(x, tol=1e-6, max_sweeps=400, x_true=xts[id(p)])
+            ts.append(ip.seconds)
+        times[cls] = float(np.median(ts))
+    per_solve = 0.95 * times["small_f32"] + 0.05 * times["large_f32"]
+    out["plain_fp32_one_at_a_time"] = {"small_ms": 1e3 * times["small_f32"],
+                                       "large_ms": 1e3 * times["large_f32"],
+                                       "solves_per_s_at_the_mix": 1.0 / per_solve}
+    for v in pool.values():
+        for p in v:
+            p.close()
+    return out
+
+
 def run_asyrk(args, dist):
     import torch
 
@@ -404,6 +612,13 @@ def run_asyrk(args, dist):
                "sample": "%d projections (%.2f sweeps) of the same system from x0=0, FP64 "
                          "oracle, single thread, %.1f s" % (nsteps, nsteps / s.m, dt)}
 
+    extras = None
+    if dist.rank == 0 and not args.no_extras:
+        extras = {"plain_and_refine": extras_plain_refine(asyrk, synth),
+                  "batched": extras_batched(asyrk, synth, torch),
+                  "served": extras_served(asyrk, synth, torch, args.served_seconds,
+                                          args.served_rate)}
+
     if dist.rank == 0:
         cfg = workload_config(s, args)
         cfg.update({"sweeps_per_step": sweeps, "workers": infos[0].workers,
@@ -417,7 +632,7 @@ def run_asyrk(args, dist):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "clocks": clock, "e2e": e2e, "gpu_launches": int(launches_all),
                 "roofline": roofline, "cpu_baseline": cpu,
-                "kernel_source_sha256": kernel_source_hash()}
+                "kernel_source_sha256": kernel_source_hash(), "extras": extras}
         print(json.dumps(line), flush=True)
 
 

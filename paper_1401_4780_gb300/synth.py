@@ -220,3 +220,57 @@ def batch_systems(count: int = 256, rep: int = 0, value_dtype: str = "f32", **sh
     base = config_seed(4, rep) * 1000
     return [make_system(m, n, L, base + k, row_norms="unit", value_dtype=value_dtype)
             for k, (m, n, L) in enumerate(shapes)]
+
+
+# ---------------------------------------------------------------------------
+# the same construction on the GPU (for benchmark inputs too large to build
+# quickly on the host); seeded with a torch generator, so it reproduces itself
+# but not the numpy systems above
+# ---------------------------------------------------------------------------
+def make_system_torch(m: int, n: int, L: int, seed: int, *, row_norms: str = "unit",
+                      value_dtype: str = "f32", device: str = "cuda"):
+    """Dict of device tensors: row_ptr (int64), col (int32), val_store (float64 /
+    float32 / int16 BF16 bits), x_true and b (float64); L distinct uniformly
+    random columns per row (ascending), N(0,1) values, rows normalized (or
+    lognormal(0,1) norms), rounded to the storage type, b = A x* in FP64 from
+    the stored values."""
+    import torch
+    if value_dtype not in VALUE_DTYPES:
+        raise ValueError(value_dtype)
+    if L > n:
+        raise ValueError("row length exceeds n")
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    cols = torch.randint(0, n, (m, L), generator=g, device=device, dtype=torch.int64)
+    cols, _ = torch.sort(cols, dim=1)
+    for _ in range(1000):
+        bad = (cols[:, 1:] == cols[:, :-1]).any(dim=1).nonzero().flatten()
+        if bad.numel() == 0:
+            break
+        redo = torch.randint(0, n, (bad.numel(), L), generator=g, device=device, dtype=torch.int64)
+        cols[bad] = torch.sort(redo, dim=1)[0]
+    else:
+        raise RuntimeError("could not draw distinct columns")
+    v = torch.randn((m, L), generator=g, device=device, dtype=torch.float64)
+    scale = 1.0 / torch.sqrt((v * v).sum(dim=1, keepdim=True))
+    if row_norms == "lognormal":
+        scale = scale * torch.exp(torch.randn((m, 1), generator=g, device=device,
+                                              dtype=torch.float64))
+    elif row_norms != "unit":
+        raise ValueError(row_norms)
+    v = v * scale
+    if value_dtype == "f64":
+        store, v64 = v, v
+    elif value_dtype == "f32":
+        store = v.to(torch.float32)
+        v64 = store.to(torch.float64)
+    else:
+        store32 = v.to(torch.bfloat16)  # round to nearest even from FP64
+        v64 = store32.to(torch.float64)
+        store = store32.view(torch.int16)
+    x_true = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+    b = (v64 * x_true[cols]).sum(dim=1)
+    row_ptr = torch.arange(0, (m + 1) * L, L, device=device, dtype=torch.int64)
+    return {"m": m, "n": n, "L": L, "row_ptr": row_ptr, "col": cols.to(torch.int32).reshape(-1),
+            "val_store": store.reshape(-1).contiguous(), "x_true": x_true, "b": b,
+            "value_dtype": value_dtype, "seed": int(seed)}
