@@ -71,6 +71,8 @@ def parse_args():
     ap.add_argument("--served-seconds", type=float, default=10.0,
                     help="length of the Poisson arrival window of the served measurement")
     ap.add_argument("--served-rate", type=float, default=2000.0, help="requests per second")
+    ap.add_argument("--served-rate2", type=float, default=1000.0,
+                    help="a second, lower offered rate (0: skip)")
     return ap.parse_args()
 
 
@@ -618,6 +620,9 @@ def run_asyrk(args, dist):
                   "batched": extras_batched(asyrk, synth, torch),
                   "served": extras_served(asyrk, synth, torch, args.served_seconds,
                                           args.served_rate)}
+        if args.served_rate2 > 0:
+            extras["served_lower_rate"] = extras_served(asyrk, synth, torch, args.served_seconds,
+                                                        args.served_rate2)
 
     if dist.rank == 0:
         cfg = workload_config(s, args)

@@ -141,9 +141,10 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
     int sms = problems[0]->sm_count;
     int st = batch_resident_warps(sms, b->excl, &b->resident_warps);
     if (st != ASYRK_OK) return fail(st);
-    if (count > b->resident_warps)
-        return fail(set_error(ASYRK_EINVAL, "%d problems exceed the %d resident warps", count,
-                              b->resident_warps));
+    if (count > b->resident_warps || count > BATCH_MAX_SLOTS)
+        return fail(set_error(ASYRK_EINVAL, "%d problems exceed the %d a batch can hold", count,
+                              b->resident_warps < BATCH_MAX_SLOTS ? b->resident_warps
+                                                                 : BATCH_MAX_SLOTS));
 
     b->h.assign(count, SysDesc());
     b->xoff.assign(count + 1, 0);
@@ -238,6 +239,8 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
         D.meas = D.meas0 = -1.0;
         D.first_nwarps = 0;
         D.nwarps = 0;
+        D.max_k = 1;  // every sweep is checked: sweep counts comparable with a single solve
+        D.k = 1;
         D.warp0 = 0;
         D.chk_count = 0;
         D.res_count = 0;

@@ -5,10 +5,11 @@
 // One iteration of the engine is four kernels:
 //   plan     split the resident warps among the active slots in proportion to
 //            their work per sweep, each capped by its concurrency limit (the
-//            tau bound of Cor. 2, expressed in warps);
-//   project  every warp finds its slot and runs that slot's workers for one
-//            sweep (m_s projections) with the slot's value type and sub-warp
-//            width (worker.cuh);
+//            tau bound of Cor. 2, expressed in warps), and let a slot whose
+//            sweep is short next to the step's longest run up to max_k sweeps;
+//   project  every warp finds its slot and runs that slot's workers for its
+//            k sweeps (k m_s projections) with the slot's value type and
+//            sub-warp width (worker.cuh);
 //   check    the slot's FP64 error measure (||x - x*|| / ||x*|| with x*, else
 //            ||b - A x|| / ||b||), its sweep count and done/status;
 //   cond     count the active slots; in a CUDA graph, set the WHILE condition.
@@ -20,6 +21,7 @@ namespace asyrk {
 
 constexpr int BATCH_ERR_CHUNK = 16384;  // x entries per check block (x* measure)
 constexpr int BATCH_ROW_CHUNK = 2048;   // rows per check block (residual measure)
+constexpr int BATCH_MAX_SLOTS = 4096;   // slots the plan kernel can place
 
 struct SysDesc {
     const RowRec *rec;
@@ -66,6 +68,8 @@ struct SysDesc {
     int outer_steps;
     unsigned out_count;   // last-block counter of the outer step
     double outer_ref;     // ||x*|| (with x*) or ||b|| for the outer measure
+    int max_k;            // sweeps one engine step may run for this slot (>= 1)
+    int k;                // sweeps this step (set by plan)
 };
 
 constexpr int SLOT_PLAIN = 0;

@@ -18,47 +18,144 @@ long long tau_cap_estimate(int64_t m, int64_t n)
 }
 
 // ---------------------------------------------------------------------------
-// plan: one thread; a handful of passes over the slots
+// plan: one block; each thread owns slots tid, tid + blockDim, ...
 // ---------------------------------------------------------------------------
-__global__ void k_batch_plan(SysDesc *d, int count, int R)
+constexpr int PLAN_THREADS = 1024;
+constexpr int PLAN_PER_THREAD = BATCH_MAX_SLOTS / PLAN_THREADS;
+
+template <typename T, typename Op>
+__device__ __forceinline__ T block_all(T v, Op op, T *sh)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double wtot = 0.0;
-    for (int s = 0; s < count; ++s)
-        if (d[s].active && d[s].phase == 0) wtot += d[s].work;
-    int used = 0;
-    for (int s = 0; s < count; ++s) {
-        int w = 0;
-        if (d[s].active && d[s].phase == 0 && wtot > 0.0) {
-            w = (int)((double)R * d[s].work / wtot);
-            if (w < 1) w = 1;
-            if (w > d[s].cap_warps) w = d[s].cap_warps;
-        }
-        d[s].nwarps = w;
-        used += w;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T r = sh[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = op(r, sh[w]);
+    __syncthreads();
+    return r;
+}
+
+// exclusive prefix sum over the block; *total receives the block's sum
+__device__ __forceinline__ long long block_excl_scan(long long v, long long *sh, long long &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
-    // hand the remainder to slots below their cap, in proportion to their work
-    for (int pass = 0; pass < 2 && used < R; ++pass) {
-        double wunc = 0.0;
-        for (int s = 0; s < count; ++s)
-            if (d[s].active && d[s].phase == 0 && d[s].nwarps < d[s].cap_warps) wunc += d[s].work;
+    __syncthreads();
+    if (lane == 31) sh[wid] = incl;
+    __syncthreads();
+    long long before = 0, tot = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        if (k < wid) before += sh[k];
+        tot += sh[k];
+    }
+    __syncthreads();
+    total = tot;
+    return before + incl - v;
+}
+
+__global__ void __launch_bounds__(PLAN_THREADS) k_batch_plan(SysDesc *d, int count, int R,
+                                                              int even_share)
+{
+    __shared__ double shd[32];
+    __shared__ long long shl[32];
+    const int tid = threadIdx.x;
+    auto add_d = [](double a, double b) { return a + b; };
+    auto max_d = [](double a, double b) { return a > b ? a : b; };
+    auto add_l = [](long long a, long long b) { return a + b; };
+    double work[PLAN_PER_THREAD], chain[PLAN_PER_THREAD];
+    int cap[PLAN_PER_THREAD], w[PLAN_PER_THREAD];
+    bool on[PLAN_PER_THREAD];
+    double wt = 0.0;
+    long long na = 0;
+#pragma unroll
+    for (int q = 0; q < PLAN_PER_THREAD; ++q) {
+        const int s = tid + q * PLAN_THREADS;
+        on[q] = s < count && d[s].active && d[s].phase == 0;
+        work[q] = on[q] ? d[s].work : 0.0;
+        cap[q] = on[q] ? (d[s].cap_warps > 0 ? d[s].cap_warps : 1) : 0;
+        // projections per worker per sweep with one warp (32/G workers)
+        chain[q] = on[q] ? (double)d[s].m / (double)(32 / (d[s].G > 0 ? d[s].G : 32)) : 0.0;
+        wt += work[q];
+        na += on[q] ? 1 : 0;
+    }
+    const double wtot = block_all(wt, add_d, shd);
+    const long long nact = block_all(na, add_l, shl);
+    // with even_share, half of the warps evenly (short, latency-bound solves get
+    // parallelism); the rest in proportion to the work per sweep.  Every active
+    // slot gets at least one warp and at most its cap; the total stays <= R.
+    long long even = nact > 0 ? 1 : 0;
+    if (even_share && nact > 0 && R / (2 * nact) > 1) even = R / (2 * nact);
+    long long u = 0;
+#pragma unroll
+    for (int q = 0; q < PLAN_PER_THREAD; ++q) {
+        w[q] = on[q] ? (int)(even < cap[q] ? even : cap[q]) : 0;
+        u += w[q];
+    }
+    long long used = block_all(u, add_l, shl);
+    for (int pass = 0; pass < 2 && used < R && wtot > 0.0; ++pass) {
+        double wu = 0.0;
+#pragma unroll
+        for (int q = 0; q < PLAN_PER_THREAD; ++q)
+            if (on[q] && w[q] < cap[q]) wu += work[q];
+        const double wunc = block_all(wu, add_d, shd);
         if (wunc <= 0.0) break;
-        const int left = R - used;
-        for (int s = 0; s < count && used < R; ++s) {
-            if (!d[s].active || d[s].phase != 0 || d[s].nwarps >= d[s].cap_warps) continue;
-            int add = (int)((double)left * d[s].work / wunc);
-            if (add > d[s].cap_warps - d[s].nwarps) add = d[s].cap_warps - d[s].nwarps;
-            if (add > R - used) add = R - used;
-            d[s].nwarps += add;
-            used += add;
+        const long long left = R - used;
+        long long a_sum = 0;
+#pragma unroll
+        for (int q = 0; q < PLAN_PER_THREAD; ++q) {
+            if (!on[q] || w[q] >= cap[q]) continue;
+            long long a = (long long)((double)left * work[q] / wunc);
+            if (a > cap[q] - w[q]) a = cap[q] - w[q];
+            w[q] += (int)a;
+            a_sum += a;
         }
+        used += block_all(a_sum, add_l, shl);
     }
-    int acc = 0;
-    for (int s = 0; s < count; ++s) {
-        if (acc + d[s].nwarps > R) d[s].nwarps = R - acc > 0 ? R - acc : 0;
-        d[s].warp0 = acc;
-        acc += d[s].nwarps;
-        if (d[s].first_nwarps == 0) d[s].first_nwarps = d[s].nwarps;  // reported workers
+    // sweeps this step: each slot's worker chain (projections per worker for
+    // its k sweeps) should not outlast the longest single-sweep chain
+    double tl = 0.0;
+#pragma unroll
+    for (int q = 0; q < PLAN_PER_THREAD; ++q)
+        if (on[q] && w[q] > 0 && chain[q] / w[q] > tl) tl = chain[q] / w[q];
+    const double tmax = block_all(tl, max_d, shd);
+    // warp ranges: exclusive prefix of the warps in slot order, one stride row
+    // (slots q*PLAN_THREADS .. q*PLAN_THREADS + PLAN_THREADS - 1) at a time
+    long long base = 0;
+#pragma unroll
+    for (int q = 0; q < PLAN_PER_THREAD; ++q) {
+        long long row_total = 0;
+        const long long ex = block_excl_scan((long long)w[q], shl, row_total);
+        const int s = tid + q * PLAN_THREADS;
+        if (s < count) {
+            long long w0 = base + ex, nw = w[q];
+            if (w0 >= R) {
+                w0 = R;
+                nw = 0;
+            } else if (w0 + nw > R) {
+                nw = R - w0;
+            }
+            int kk = 1;
+            if (on[q] && nw > 0 && tmax > 0.0) {
+                const double kf = tmax / (chain[q] / (double)nw);
+                long long kmax = d[s].max_k > 1 ? d[s].max_k : 1;
+                const long long left_sw = d[s].max_sweeps - d[s].sweeps;
+                if (kmax > left_sw) kmax = left_sw > 1 ? left_sw : 1;
+                kk = kf >= (double)kmax ? (int)kmax : (kf < 1.0 ? 1 : (int)kf);
+            }
+            d[s].warp0 = (int)w0;
+            d[s].nwarps = (int)nw;
+            d[s].k = kk;
+            if (d[s].first_nwarps == 0) d[s].first_nwarps = (int)nw;  // reported workers
+        }
+        base += row_total;
     }
 }
 
@@ -134,7 +231,7 @@ __global__ void __launch_bounds__(256) k_batch_project(SysDesc *d, int count)
     a.uniform = D.uniform;
     a.stream_id = D.stream_id;
     a.j0 = D.j;
-    a.count = D.m;  // one sweep
+    a.count = (unsigned long long)D.m * (unsigned long long)(D.k > 1 ? D.k : 1);  // k sweeps
     a.workers = (long long)D.nwarps * (32 / D.G);
     a.gamma = (double)D.gamma;
     a.bvec = D.bvec;
@@ -269,11 +366,12 @@ __global__ void __launch_bounds__(256) k_batch_check(SysDesc *d, int count, doub
         }
         return;
     }
-    D.j += D.m;
-    D.sweeps += 1;
+    const int ksw = D.k > 1 ? D.k : 1;
+    D.j += (unsigned long long)D.m * (unsigned long long)ksw;
+    D.sweeps += ksw;
     if (D.meas0 < 0.0) D.meas0 = meas;  // slots started without a first measure
     if (D.mode == SLOT_REFINE) {  // inner solve of A d = r: hand over to the outer step
-        D.inner_sweeps += 1;
+        D.inner_sweeps += ksw;
         if (!isfinite(meas)) {
             D.active = 0;
             D.status = ASYRK_DIVERGED;
@@ -446,7 +544,9 @@ int batch_resident_warps(int sm_count, bool excl, int *warps)
 int launch_engine_step(SysDesc *d, int count, int total_chunks, double *part, int resident_warps,
                        bool excl, bool with_outer, cudaStream_t s)
 {
-    k_batch_plan<<<1, 32, 0, s>>>(d, count, resident_warps);
+    // the server (with_outer) splits half of the warps evenly; a batch, whose
+    // members all run to the end of the same iteration, splits by work only
+    k_batch_plan<<<1, PLAN_THREADS, 0, s>>>(d, count, resident_warps, with_outer ? 1 : 0);
     ASYRK_CK(cudaGetLastError());
     const unsigned blocks = (unsigned)((resident_warps + 7) / 8);
     if (excl)

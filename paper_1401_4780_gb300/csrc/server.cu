@@ -291,6 +291,7 @@ static bool admit_locked(asyrk_server *sv, Request *r, int k)
     D.outer_ref = D.ref;
     D.inner_tol = sv->inner_tol;
     D.max_inner = sv->max_inner;
+    D.max_k = 32;  // short sweeps run several per engine step
     sv->slot_req[k] = r;
     r->slot = k;
     r->t_admit = now_s();
@@ -491,6 +492,7 @@ extern "C" int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *
     if (st != ASYRK_OK) return fail(st);
     sv->max_slots = o.max_slots > 0 ? o.max_slots : 256;
     if (sv->max_slots > sv->resident_warps) sv->max_slots = sv->resident_warps;
+    if (sv->max_slots > BATCH_MAX_SLOTS) sv->max_slots = BATCH_MAX_SLOTS;
     sv->h.assign(sv->max_slots, SysDesc());
     memset(sv->h.data(), 0, sv->max_slots * sizeof(SysDesc));
     sv->slot_req.assign(sv->max_slots, nullptr);
