@@ -50,7 +50,7 @@ UNIT = "row projections/s"
 BYTES_PER_PROJECTION = 32 * 8 + 16 + 8
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_project_large_async.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1401_4780_gb300", "csrc", f)
-                  for f in ("project.cu", "common.cuh")]
+                  for f in ("project.cu", "worker.cuh", "common.cuh")]
 
 
 def parse_args():
@@ -565,9 +565,10 @@ def run_asyrk(args, dist):
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "kernel": "k_project<float,float,8> (one sweep per launch)",
-                "binding": "L2 request rate: ~64 random 4-byte gathers/red.adds per projection on "
-                           "the L2-resident x (ncu: lts__t_tag_requests 78% of peak, DRAM 6%); "
-                           "see l2.frac_of_probe_pairs",
+                "binding": "L2: ~64 random 4-byte gathers/red.adds per projection on the "
+                           "L2-resident x, and their latency (ncu: L2 tag requests ~73% of "
+                           "peak, DRAM ~8%, long-scoreboard stalls); DRAM traffic per launch "
+                           "is ~1.04x the algorithmic bytes",
                 "bytes_per_projection": BYTES_PER_PROJECTION,
                 "projections_per_launch": per_launch_proj,
                 "launch_ms": per_launch_s * 1e3,

@@ -12,7 +12,7 @@
 namespace asyrk {
 
 template <typename VT, typename XT, int G, bool SEQ, bool EXCL>
-__global__ void __launch_bounds__(256) k_project(const ProjArgs a)
+__global__ void __launch_bounds__(256, 4) k_project(const ProjArgs a)  // <= 64 registers
 {
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long skipped = run_workers<VT, XT, G, SEQ, EXCL>(a, warp * (32 / G),

@@ -107,17 +107,22 @@ __device__ __forceinline__ void scatter4(const XT (&v)[4], int4 c, int k, XT s, 
 }
 
 // Row exclusion: a worker claims its row in a bitmask (one bit per row, at
-// L2) with an acquire atomic OR before gathering x, and releases it with a
-// release AND after its updates.  A row already claimed is skipped: no row is
-// ever applied twice from the same stale x, the property the paper's
-// implementation gets from giving each thread its own rows (Section 5).  The
-// skipped projection would, in the sequential order, come right after the
-// same projection and change x only through the few updates in between
-// (projections are idempotent).
+// L2) with an atomic OR before gathering x, and clears the bit after issuing
+// its updates; a row whose bit is already set is skipped.  So no row is held
+// by two workers at once -- many copies of one (heavily weighted) row would
+// apply the same correction again and again from the same stale x -- the
+// property the paper's implementation gets from giving each thread its own
+// rows (Section 5).  The skipped projection would, in the sequential order,
+// come right after the same projection and change x only through the few
+// updates in between (projections are idempotent).
+// Both operations are relaxed: the next holder may still read x before the
+// previous holder's red.adds have landed, the same bounded staleness every
+// read of x has.  Release ordering would make the clearing lane wait for all
+// of its outstanding red.adds, which costs about a fifth of the throughput.
 __device__ __forceinline__ unsigned claim_row(unsigned *busy, unsigned i)
 {
     unsigned old;
-    asm volatile("atom.acquire.gpu.global.or.b32 %0, [%1], %2;"
+    asm volatile("atom.relaxed.gpu.global.or.b32 %0, [%1], %2;"
                  : "=r"(old)
                  : "l"(busy + (i >> 5)), "r"(1u << (i & 31))
                  : "memory");
@@ -126,15 +131,11 @@ __device__ __forceinline__ unsigned claim_row(unsigned *busy, unsigned i)
 
 __device__ __forceinline__ void release_row(unsigned *busy, unsigned i)
 {
-    asm volatile("red.release.gpu.global.and.b32 [%0], %1;" ::"l"(busy + (i >> 5)),
+    asm volatile("red.relaxed.gpu.global.and.b32 [%0], %1;" ::"l"(busy + (i >> 5)),
                  "r"(~(1u << (i & 31)))
                  : "memory");
 }
 
-// One persistent worker group's share of a launch: worker gbase + sub (sub <
-// 32/G) applies projections t = worker, worker + W, ... < a.count.  Called by
-// every lane of a warp with the same gbase; returns the projections this lane
-// skipped by row exclusion (counted on group leaders only).
 template <typename VT, typename XT, int G, bool SEQ, bool EXCL>
 __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, long long gbase,
                                                           long long W)
@@ -187,7 +188,6 @@ __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, lon
         if (EXCL) {
             unsigned got = 0;
             if (act && sl == 0) got = claim_row(a.busy, i);
-            __syncwarp();  // orders the leader's acquire before the group's gathers
             got = __shfl_sync(0xffffffffu, got, lane & ~(G - 1));
             if (act && !got) {
                 act = false;
@@ -230,7 +230,7 @@ __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, lon
             }
         }
         if (EXCL) {
-            __syncwarp();  // the group's updates happen before the leader's release
+            __syncwarp();  // the group's updates are issued before the bit is cleared
             if (act && sl == 0) release_row(a.busy, i);
         }
         if (SEQ) {
