@@ -15,6 +15,10 @@ __device__ __forceinline__ unsigned xs32(unsigned &s)
     return s;
 }
 
+// Each thread issues P independent operations per loop trip so that the probe
+// is limited by the memory system, not by the latency of one thread's chain.
+constexpr int P = 8;
+
 template <int KIND>
 __global__ void __launch_bounds__(256) k_probe(float *a, unsigned n, long long ops, float *sink)
 {
@@ -31,14 +35,34 @@ __global__ void __launch_bounds__(256) k_probe(float *a, unsigned n, long long o
             acc += t.x + t.y + t.z + t.w;
         }
     } else {
-        for (long long k = tid; k < ops; k += nth) {
-            const unsigned i = __umulhi(xs32(s), n);
-            if (KIND == ASYRK_PROBE_GATHER_F32 || KIND == ASYRK_PROBE_GATHER_RED)
-                acc += __ldcg(a + i);
-            if (KIND == ASYRK_PROBE_RED_F32 || KIND == ASYRK_PROBE_GATHER_RED) {
-                const unsigned j = __umulhi(xs32(s), n);
-                asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(a + j), "f"(1e-30f)
-                             : "memory");
+        // ops counts single operations (pairs for GATHER_RED)
+        for (long long k = tid * P; k < ops; k += nth * P) {
+            unsigned idx[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) idx[q] = __umulhi(xs32(s), n);
+            if (KIND == ASYRK_PROBE_RED_F32) {
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(a + idx[q]),
+                                 "f"(1e-30f)
+                                 : "memory");
+            } else {
+                float g[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) g[q] = __ldcg(a + idx[q]);
+                float r = 0.f;
+#pragma unroll
+                for (int q = 0; q < P; ++q) r += g[q];
+                if (KIND == ASYRK_PROBE_GATHER_F32) {
+                    acc += r;
+                } else {  // the projection's pattern: reduce, then update the same entries
+                    const float sc = 1e-30f * r;
+#pragma unroll
+                    for (int q = 0; q < P; ++q)
+                        asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(a + idx[q]),
+                                     "f"(sc)
+                                     : "memory");
+                }
             }
         }
     }
