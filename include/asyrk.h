@@ -83,6 +83,15 @@ typedef enum asyrk_mode {
     ASYRK_MODE_REFINE = 2
 } asyrk_mode;
 
+typedef enum asyrk_measure {
+    /* ||x - x*|| / ||x*|| when x_true is given, else ||b - A x|| / ||b||  */
+    ASYRK_MEASURE_AUTO = 0,
+    /* ||b - A x|| / ||b|| (Section 5's figures plot ||Ax - b||)          */
+    ASYRK_MEASURE_RESIDUAL = 1,
+    /* ||A^T (A x - b)||^2, absolute (the measure of Table 2)            */
+    ASYRK_MEASURE_NORMAL_RESIDUAL = 2
+} asyrk_measure;
+
 typedef struct asyrk_create_opts {
     uint64_t seed;       /* Philox key of the row sequence                       */
     int32_t device_ptrs; /* 1: row_ptr, col_idx, values, b are device pointers  */
@@ -94,7 +103,7 @@ typedef struct asyrk_solve_opts {
     int32_t mode;            /* asyrk_mode                                           */
     int32_t device_ptrs;     /* 1: x and x_true are device pointers (double)         */
     int32_t workers;         /* concurrent row workers; 0 = automatic (ASYNC/REFINE)  */
-    int32_t subwarp;         /* lanes per row: 0 = automatic, or 2, 4, 8, 16, 32      */
+    int32_t subwarp;         /* lanes per row: 0 = automatic, or 1, 2, 4, 8, 16, 32   */
     int64_t check_every;     /* sweeps between convergence checks; >= 1              */
     const double *x_true;    /* optional x*; checks then use ||x-x*||/||x*||          */
     void *stream;            /* cudaStream_t; NULL = legacy default stream           */
@@ -105,6 +114,8 @@ typedef struct asyrk_solve_opts {
                                 worker is applying (default); -1 = plain lock-free
                                 updates, where one row may be applied several times
                                 from the same stale x                                 */
+    int32_t measure;         /* asyrk_measure of the convergence check               */
+    int32_t reserved2;       /* must be 0                                            */
 } asyrk_solve_opts;
 
 typedef struct asyrk_solve_info {
@@ -174,6 +185,10 @@ int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol, int64_t m
  * x: n doubles, host or device (x_on_device).  Errors: EINVAL, ECUDA. */
 int asyrk_residual(asyrk_problem *p, const double *x, int x_on_device, double *rel_residual);
 
+/* ||A^T (A x - b)||^2 in FP64 on the GPU (the measure of Table 2); x: n
+ * doubles, host or device.  Errors: EINVAL, ENOMEM, ECUDA. */
+int asyrk_normal_residual(asyrk_problem *p, const double *x, int x_on_device, double *value);
+
 /* The rows drawn by projections j0 .. j0+count-1 with Philox stream id
  * `stream_id`, computed by the GPU sampler that the projection kernels use;
  * rows_out: count int32 on the host.  Errors: EINVAL (count < 0), ECUDA. */
@@ -191,7 +206,7 @@ int asyrk_problem_get_stats(asyrk_problem *p, asyrk_problem_stats *stats);
 
 /* ------------------------------------------------------------------------
  * Autotuner (not in the paper).  Times the projection kernel on problem p for
- * every sub-warp width (2..32 lanes per row) and for 1/2, 3/4 and all of the
+ * every sub-warp width (1..32 lanes per row) and for 1/2, 3/4 and all of the
  * resident workers (never above the Cor. 2 worker estimate m / (2 e
  * lambda_max) - 1 with lambda_max ~ (1 + sqrt(m/n))^2, Section 1), each for
  * `trial_projections` projections (0: min(2m, 2^22)) on a scratch iterate;

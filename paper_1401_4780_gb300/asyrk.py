@@ -20,6 +20,7 @@ F64, F32, BF16 = 0, 1, 2
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_CONVERGED, DIVERGED = 0, -1, -2, -3, -4, 1, 2
 ECANCELED = -5
 MODE_SEQUENTIAL, MODE_ASYNC, MODE_REFINE = 0, 1, 2
+MEASURE_AUTO, MEASURE_RESIDUAL, MEASURE_NORMAL_RESIDUAL = 0, 1, 2
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
 
 
@@ -41,7 +42,8 @@ class SolveOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int64), ("x_true", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("inner_tol", ctypes.c_double),
                 ("inner_sweeps", ctypes.c_int64), ("profile", ctypes.c_int32),
-                ("row_exclusion", ctypes.c_int32)]
+                ("row_exclusion", ctypes.c_int32), ("measure", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -71,7 +73,7 @@ class ProblemStats(ctypes.Structure):
 EXPORTS = ["asyrk_create", "asyrk_destroy", "asyrk_solve", "asyrk_residual", "asyrk_draw_rows",
            "asyrk_get_position", "asyrk_set_position", "asyrk_problem_get_stats",
            "asyrk_strerror", "asyrk_last_error", "asyrk_abi_version", "asyrk_probe",
-           "asyrk_residual_noalloc", "asyrk_autotune", "asyrk_batch_create", "asyrk_batch_solve",
+           "asyrk_residual_noalloc", "asyrk_normal_residual", "asyrk_autotune", "asyrk_batch_create", "asyrk_batch_solve",
            "asyrk_batch_destroy", "asyrk_server_create", "asyrk_server_submit",
            "asyrk_server_wait", "asyrk_server_cancel", "asyrk_server_get_stats",
            "asyrk_server_destroy"]
@@ -101,6 +103,8 @@ def load(path: str = LIB_PATH):
     lib.asyrk_solve.restype = ctypes.c_int
     lib.asyrk_residual.argtypes = [P, P, ctypes.c_int, ctypes.POINTER(f64)]
     lib.asyrk_residual.restype = ctypes.c_int
+    lib.asyrk_normal_residual.argtypes = [P, P, ctypes.c_int, ctypes.POINTER(f64)]
+    lib.asyrk_normal_residual.restype = ctypes.c_int
     lib.asyrk_draw_rows.argtypes = [P, u64, i64, u32, P]
     lib.asyrk_draw_rows.restype = ctypes.c_int
     lib.asyrk_get_position.argtypes = [P, ctypes.POINTER(u64)]
@@ -257,6 +261,12 @@ def asyrk_residual(h, x, x_on_device=False):
     return st, out.value
 
 
+def asyrk_normal_residual(h, x, x_on_device=False):
+    out = ctypes.c_double()
+    st = load().asyrk_normal_residual(h, _ptr(x), 1 if x_on_device else 0, ctypes.byref(out))
+    return st, out.value
+
+
 def asyrk_draw_rows(h, j0, count, stream_id=0):
     rows = np.zeros(count, dtype=np.int32)
     st = load().asyrk_draw_rows(h, j0, count, stream_id, _ptr(rows))
@@ -381,11 +391,13 @@ def asyrk_problem_get_stats(h):
 # owner object
 # ---------------------------------------------------------------------------
 def solve_opts(mode=MODE_ASYNC, workers=0, subwarp=0, check_every=1, x_true=None, stream=None,
-               inner_tol=0.0, inner_sweeps=0, profile=False, device_ptrs=False, row_exclusion=0):
+               inner_tol=0.0, inner_sweeps=0, profile=False, device_ptrs=False, row_exclusion=0,
+               measure=MEASURE_AUTO):
     return SolveOpts(mode=mode, device_ptrs=1 if device_ptrs else 0, workers=workers,
                      subwarp=subwarp, check_every=check_every, x_true=_ptr(x_true),
                      stream=_stream(stream), inner_tol=inner_tol, inner_sweeps=inner_sweeps,
-                     profile=1 if profile else 0, row_exclusion=row_exclusion)
+                     profile=1 if profile else 0, row_exclusion=row_exclusion, measure=measure,
+                     reserved2=0)
 
 
 class Problem:
@@ -438,6 +450,13 @@ class Problem:
         st, r = asyrk_residual(self.h, x, x_on_device)
         if st != OK:
             raise AsyrkError(st, "asyrk_residual")
+        return r
+
+    def normal_residual(self, x, x_on_device=False):
+        """||A^T (A x - b)||^2 (Table 2's measure), FP64 on the GPU."""
+        st, r = asyrk_normal_residual(self.h, x, x_on_device)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_normal_residual")
         return r
 
     def draw_rows(self, j0, count, stream_id=0):

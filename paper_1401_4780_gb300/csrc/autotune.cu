@@ -1,7 +1,7 @@
 // autotune.cu -- asyrk_autotune: choose the projection kernel's launch shape by
 // timing it on the problem itself.
 //
-// The shape is the sub-warp width G (lanes per row, hence 32/G rows per warp)
+// The shape is the sub-warp width G (1..32 lanes per row, hence 32/G rows per warp)
 // and the number of concurrent workers W.  W never exceeds the Cor. 2
 // estimate of how many workers keep the rate near the sequential one; within
 // that, the fastest measured shape wins.  Results are kept per (value dtype,
@@ -49,7 +49,7 @@ static void load_locked()
     long long lc;
     double frac, rate;
     while (fscanf(f, "%d %lld %d %d %lf %lf", &dt, &lc, &sms, &G, &frac, &rate) == 6)
-        if (G >= 2 && G <= 32 && (G & (G - 1)) == 0 && frac > 0.0 && frac <= 1.0)
+        if (G >= 1 && G <= 32 && (G & (G - 1)) == 0 && frac > 0.0 && frac <= 1.0)
             g_tune[TuneKey(dt, lc, sms)] = TuneVal{G, frac, rate};
     fclose(f);
 }
@@ -130,7 +130,7 @@ extern "C" int asyrk_autotune(asyrk_problem *p, int64_t trial, int force, asyrk_
     int bestG = 0, bestW = 0;
     double bestFrac = 1.0;
     const double fracs[3] = {0.5, 0.75, 1.0};
-    for (int g = 2; g <= 32; g *= 2) {
+    for (int g = 1; g <= 32; g *= 2) {
         // rows must fit the registers (two 4G-entry chunks) unless g is the widest
         if (8LL * g < p->max_len && g < 32) continue;
         // and should not leave most lanes idle

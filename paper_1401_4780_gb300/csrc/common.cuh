@@ -59,6 +59,7 @@ struct asyrk_problem {
     void *xw = nullptr;          // n x {float|double}: the shared iterate
     double *x64 = nullptr;       // n: FP64 iterate / staging
     double *xt64 = nullptr;      // n: x*
+    double *g64 = nullptr;       // n: A^T (A x - b) (Table 2's measure), allocated on use
     double *red_part = nullptr;  // reduction partials
     unsigned *red_count = nullptr;
     double *red_out = nullptr;   // 8 result slots
@@ -165,6 +166,8 @@ int launch_draw_rows(const asyrk_problem *p, unsigned long long j0, int64_t coun
 int launch_err2(asyrk_problem *p, const void *x, bool x_f64, const double *xt, int slot,
                 cudaStream_t s);
 int launch_sumsq(asyrk_problem *p, const double *v, int64_t n, int slot, cudaStream_t s);
+// ||A^T (A x - b)||^2 in FP64 into red_out[slot]
+int launch_normal_residual(asyrk_problem *p, const void *x, bool x_f64, int slot, cudaStream_t s);
 int launch_residual(asyrk_problem *p, const void *x, bool x_f64, bool write_rec_b, int slot,
                     cudaStream_t s);
 int launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t n,

@@ -203,6 +203,7 @@ template <typename VT, bool EXCL>
 __device__ __forceinline__ unsigned long long batch_run_g(const ProjArgs &a, int G, int rel_warp)
 {
     switch (G) {
+    case 1: return batch_run<VT, 1, EXCL>(a, rel_warp);
     case 2: return batch_run<VT, 2, EXCL>(a, rel_warp);
     case 4: return batch_run<VT, 4, EXCL>(a, rel_warp);
     case 8: return batch_run<VT, 8, EXCL>(a, rel_warp);

@@ -137,6 +137,43 @@ __global__ void __launch_bounds__(RT) k_residual(const RowRec *rec,
     block_finish<1>(v, part, count, out);
 }
 
+// g += A^T (A x - b), FP64: 8 lanes per row form r_i = a_i^T x - b_i, then each
+// lane adds r_i * A_it into g_t with an FP64 atomic (the measure of Table 2 is
+// ||g||^2).
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(RT) k_normal_scatter(const RowRec *__restrict__ rec,
+                                                       const int32_t *__restrict__ col,
+                                                       const VT *__restrict__ val,
+                                                       const double *__restrict__ b64,
+                                                       const XT *__restrict__ x, int64_t m,
+                                                       double *g)
+{
+    constexpr int G = 8;
+    const int lane = threadIdx.x & 31, sl = lane % G;
+    const int64_t grp = ((int64_t)blockIdx.x * RT + threadIdx.x) / G;
+    const int64_t ngrp = (int64_t)gridDim.x * RT / G;
+    const int64_t iters = (m + ngrp - 1) / ngrp;  // uniform trip count for the shuffles
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t i = grp + it * ngrp;
+        double acc = 0.0;
+        RowRec r;
+        r.len = 0;
+        r.start = 0;
+        if (i < m) {
+            r = rec[i];
+            for (int64_t k = sl; k < (int64_t)r.len; k += G)
+                acc += widen_v(val, r.start + k) * widen_x(x, col[r.start + k]);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (i < m) {
+            const double ri = acc - b64[i];
+            for (int64_t k = sl; k < (int64_t)r.len; k += G)
+                atomicAdd(g + col[r.start + k], widen_v(val, r.start + k) * ri);
+        }
+    }
+}
+
 __global__ void k_convert_f64_f32(const double *__restrict__ s, float *__restrict__ d, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -226,6 +263,39 @@ int launch_residual(asyrk_problem *p, const void *x, bool x_f64, bool write_rec_
     p->launches += 1;
     if (write_rec_b) p->rec_b_is_residual = true;
     return ASYRK_OK;
+}
+
+template <typename VT>
+static void normal_vt(asyrk_problem *p, const void *x, bool x_f64, unsigned g, cudaStream_t s)
+{
+    const VT *val = (const VT *)p->val;
+    if (x_f64)
+        k_normal_scatter<VT, double><<<g, RT, 0, s>>>(p->rec, p->col, val, p->b64,
+                                                      (const double *)x, p->m, p->g64);
+    else
+        k_normal_scatter<VT, float><<<g, RT, 0, s>>>(p->rec, p->col, val, p->b64,
+                                                     (const float *)x, p->m, p->g64);
+}
+
+int launch_normal_residual(asyrk_problem *p, const void *x, bool x_f64, int slot, cudaStream_t s)
+{
+    if (!p->g64) {
+        ASYRK_CK(cudaMalloc((void **)&p->g64, p->n * sizeof(double)));
+        p->dev_bytes += p->n * (int64_t)sizeof(double);
+    }
+    ASYRK_CK(cudaMemsetAsync(p->g64, 0, p->n * sizeof(double), s));
+    int64_t g = (p->m * 8 + RT - 1) / RT;
+    const int64_t cap = (int64_t)p->sm_count * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    switch (p->dtype) {
+    case ASYRK_F64: normal_vt<double>(p, x, x_f64, (unsigned)g, s); break;
+    case ASYRK_F32: normal_vt<float>(p, x, x_f64, (unsigned)g, s); break;
+    default: normal_vt<bf16_t>(p, x, x_f64, (unsigned)g, s); break;
+    }
+    ASYRK_CK(cudaGetLastError());
+    p->launches += 1;
+    return launch_sumsq(p, p->g64, p->n, slot, s);
 }
 
 int launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int64_t n,

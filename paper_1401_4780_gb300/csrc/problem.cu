@@ -241,6 +241,7 @@ static void free_problem(asyrk_problem *p)
     cudaFree(p->xw);
     cudaFree(p->x64);
     cudaFree(p->xt64);
+    cudaFree(p->g64);
     cudaFree(p->red_part);
     cudaFree(p->red_count);
     cudaFree(p->red_out);

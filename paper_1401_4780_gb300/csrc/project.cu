@@ -39,6 +39,7 @@ template <typename VT, typename XT, bool SEQ, bool EXCL>
 static KernelFn pick_g(int G)
 {
     switch (G) {
+    case 1: return k_project<VT, XT, 1, SEQ, EXCL>;
     case 2: return k_project<VT, XT, 2, SEQ, EXCL>;
     case 4: return k_project<VT, XT, 4, SEQ, EXCL>;
     case 8: return k_project<VT, XT, 8, SEQ, EXCL>;

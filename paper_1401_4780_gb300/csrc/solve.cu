@@ -27,10 +27,13 @@ static double now_s()
 
 static long long tau_cap(const asyrk_problem *p) { return tau_cap_estimate(p->m, p->n); }
 
+enum { MEAS_ERR = 0, MEAS_RES = 1, MEAS_NORMAL = 2 };
+
 struct SolveCtx {
     asyrk_problem *p;
     cudaStream_t s;
     bool have_xt;
+    int kind;       // MEAS_ERR: ||x-x*||/||x*||, MEAS_RES: ||b-Ax||/||b||, MEAS_NORMAL: ||A^T(Ax-b)||^2
     double ref;     // ||x*|| or ||b||
     bool profile;
     double project_ms = 0.0;
@@ -58,12 +61,13 @@ static int project(SolveCtx &c, const ProjectLaunch &L)
 static int measure(SolveCtx &c, const void *x, bool x_f64, double *out)
 {
     asyrk_problem *p = c.p;
-    int st = c.have_xt ? launch_err2(p, x, x_f64, p->xt64, 0, c.s)
-                       : launch_residual(p, x, x_f64, false, 0, c.s);
+    int st = c.kind == MEAS_ERR   ? launch_err2(p, x, x_f64, p->xt64, 0, c.s)
+             : c.kind == MEAS_RES ? launch_residual(p, x, x_f64, false, 0, c.s)
+                                  : launch_normal_residual(p, x, x_f64, 0, c.s);
     if (st != ASYRK_OK) return st;
     ASYRK_CK(cudaMemcpyAsync(p->h_out, p->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
     ASYRK_CK(cudaStreamSynchronize(c.s));
-    *out = sqrt(p->h_out[0]) / c.ref;
+    *out = c.kind == MEAS_NORMAL ? p->h_out[0] : sqrt(p->h_out[0]) / c.ref;
     return ASYRK_OK;
 }
 
@@ -194,11 +198,16 @@ static int solve_refine(SolveCtx &c, double gamma, double tol, int64_t max_sweep
     for (;;) {
         // r = b - A x64 in FP64, stored as the inner right-hand side
         if ((st = launch_residual(p, p->x64, true, true, 0, c.s)) != ASYRK_OK) return st;
-        if (c.have_xt && (st = launch_err2(p, p->x64, true, p->xt64, 2, c.s)) != ASYRK_OK) return st;
+        if (c.kind == MEAS_ERR && (st = launch_err2(p, p->x64, true, p->xt64, 2, c.s)) != ASYRK_OK)
+            return st;
+        if (c.kind == MEAS_NORMAL && (st = launch_normal_residual(p, p->x64, true, 2, c.s)) != ASYRK_OK)
+            return st;
         ASYRK_CK(cudaMemcpyAsync(p->h_out, p->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
         ASYRK_CK(cudaStreamSynchronize(c.s));
         const double rnorm = sqrt(p->h_out[0]);
-        meas = c.have_xt ? sqrt(p->h_out[2]) / c.ref : rnorm / c.ref;
+        meas = c.kind == MEAS_ERR   ? sqrt(p->h_out[2]) / c.ref
+               : c.kind == MEAS_RES ? rnorm / c.ref
+                                    : p->h_out[2];
         if (meas0 < 0.0) meas0 = meas;
         if (diverged(meas, meas0)) { status = ASYRK_DIVERGED; break; }
         if (tol > 0.0 && meas <= tol) { status = ASYRK_OK; break; }
@@ -274,11 +283,14 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
         return set_error(ASYRK_EINVAL, "unknown mode %d", o.mode);
     if (o.check_every < 1) return set_error(ASYRK_EINVAL, "check_every must be >= 1");
     if (o.workers < 0) return set_error(ASYRK_EINVAL, "workers < 0");
-    if (o.subwarp != 0 && o.subwarp != 2 && o.subwarp != 4 && o.subwarp != 8 &&
+    if (o.subwarp != 0 && o.subwarp != 1 && o.subwarp != 2 && o.subwarp != 4 && o.subwarp != 8 &&
         o.subwarp != 16 && o.subwarp != 32)
-        return set_error(ASYRK_EINVAL, "subwarp must be 0, 2, 4, 8, 16 or 32");
+        return set_error(ASYRK_EINVAL, "subwarp must be 0, 1, 2, 4, 8, 16 or 32");
     if (o.row_exclusion < -1 || o.row_exclusion > 1)
         return set_error(ASYRK_EINVAL, "row_exclusion must be -1, 0 or 1");
+    if (o.measure < ASYRK_MEASURE_AUTO || o.measure > ASYRK_MEASURE_NORMAL_RESIDUAL)
+        return set_error(ASYRK_EINVAL, "unknown measure %d", o.measure);
+    if (o.reserved2 != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
     if (o.mode == ASYRK_MODE_SEQUENTIAL && o.workers > 1)
         return set_error(ASYRK_EINVAL, "SEQUENTIAL mode has one worker");
 
@@ -293,15 +305,17 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
     const cudaMemcpyKind in_kind = o.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     ASYRK_CK(cudaMemcpyAsync(p->x64, x, p->n * sizeof(double), in_kind, c.s));
     c.have_xt = o.x_true != nullptr;
+    c.kind = o.measure == ASYRK_MEASURE_NORMAL_RESIDUAL ? MEAS_NORMAL
+             : (o.measure == ASYRK_MEASURE_RESIDUAL || !c.have_xt) ? MEAS_RES
+                                                                   : MEAS_ERR;
     if (c.have_xt) {
         ASYRK_CK(cudaMemcpyAsync(p->xt64, o.x_true, p->n * sizeof(double), in_kind, c.s));
         if ((st = launch_sumsq(p, p->xt64, p->n, 4, c.s)) != ASYRK_OK) return st;
         ASYRK_CK(cudaMemcpyAsync(p->h_out + 4, p->red_out + 4, sizeof(double), cudaMemcpyDeviceToHost, c.s));
         ASYRK_CK(cudaStreamSynchronize(c.s));
         c.ref = sqrt(p->h_out[4]);
-    } else {
-        c.ref = p->bnorm;
     }
+    if (c.kind != MEAS_ERR) c.ref = p->bnorm;
     if (!(c.ref > 0.0)) c.ref = 1.0;
 
     int status = (o.mode == ASYRK_MODE_REFINE) ? solve_refine(c, gamma, tol, max_sweeps, o, info)
@@ -350,7 +364,22 @@ extern "C" int asyrk_residual(asyrk_problem *p, const double *x, int x_on_device
     c.p = p;
     c.s = 0;
     c.have_xt = false;
+    c.kind = MEAS_RES;
     c.ref = 1.0;
     c.profile = false;
     return final_residual(c, p->x64, rel_residual);
+}
+
+extern "C" int asyrk_normal_residual(asyrk_problem *p, const double *x, int x_on_device,
+                                     double *value)
+{
+    if (!p || !x || !value) return set_error(ASYRK_EINVAL, "NULL argument");
+    int st = ensure_workspace(p);
+    if (st != ASYRK_OK) return st;
+    ASYRK_CK(cudaMemcpy(p->x64, x, p->n * sizeof(double),
+                        x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    if ((st = launch_normal_residual(p, p->x64, true, 0, 0)) != ASYRK_OK) return st;
+    ASYRK_CK(cudaMemcpy(p->h_out, p->red_out, sizeof(double), cudaMemcpyDeviceToHost));
+    *value = p->h_out[0];
+    return ASYRK_OK;
 }

@@ -124,8 +124,10 @@ def make_system(m: int, n: int, nnz_per_row, seed: int, *, row_norms: str = "uni
                 value_dtype: str = "f64", x_true=None) -> System:
     """Random sparse consistent system.
 
-    ``nnz_per_row``: an int (every row) or a (lo, hi) pair (each row's length
-    drawn uniformly in [lo, hi]).  ``row_norms``: ``"unit"`` (rows normalized,
+    ``nnz_per_row``: an int (every row), a (lo, hi) pair (each row's length
+    drawn uniformly in [lo, hi]) or ("poisson", mean): each row's length drawn
+    from Poisson(mean), at least 1 -- the row counts of Section 5's generator,
+    which places delta*m*n nonzeros at random positions (mean = delta*n).  ``row_norms``: ``"unit"`` (rows normalized,
     Section 5) or ``"lognormal"`` (row 2-norms exp(N(0,1)), so rows are not
     equally likely).
     """
@@ -139,8 +141,11 @@ def make_system(m: int, n: int, nnz_per_row, seed: int, *, row_norms: str = "uni
         col = cols.reshape(-1)
         del cols
     else:
-        lo, hi = int(nnz_per_row[0]), int(nnz_per_row[1])
-        lengths = rng.integers(lo, hi + 1, size=m).astype(np.int64)
+        if nnz_per_row[0] == "poisson":
+            lengths = np.clip(rng.poisson(float(nnz_per_row[1]), size=m), 1, n).astype(np.int64)
+        else:
+            lo, hi = int(nnz_per_row[0]), int(nnz_per_row[1])
+            lengths = rng.integers(lo, hi + 1, size=m).astype(np.int64)
         parts = []
         for L in np.unique(lengths):
             idx = np.nonzero(lengths == L)[0]
@@ -227,31 +232,47 @@ def batch_systems(count: int = 256, rep: int = 0, value_dtype: str = "f32", **sh
 # quickly on the host); seeded with a torch generator, so it reproduces itself
 # but not the numpy systems above
 # ---------------------------------------------------------------------------
-def make_system_torch(m: int, n: int, L: int, seed: int, *, row_norms: str = "unit",
+def make_system_torch(m: int, n: int, L, seed: int, *, row_norms: str = "unit",
                       value_dtype: str = "f32", device: str = "cuda"):
     """Dict of device tensors: row_ptr (int64), col (int32), val_store (float64 /
     float32 / int16 BF16 bits), x_true and b (float64); L distinct uniformly
-    random columns per row (ascending), N(0,1) values, rows normalized (or
+    random columns per row (ascending) -- L an int, or ("poisson", mean) for
+    Poisson(mean) row lengths (at least 1) --, N(0,1) values, rows normalized (or
     lognormal(0,1) norms), rounded to the storage type, b = A x* in FP64 from
     the stored values."""
     import torch
     if value_dtype not in VALUE_DTYPES:
         raise ValueError(value_dtype)
-    if L > n:
-        raise ValueError("row length exceeds n")
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
-    cols = torch.randint(0, n, (m, L), generator=g, device=device, dtype=torch.int64)
-    cols, _ = torch.sort(cols, dim=1)
+    if isinstance(L, (tuple, list)):
+        if L[0] != "poisson":
+            raise ValueError(L)
+        lengths = torch.poisson(torch.full((m,), float(L[1]), device=device, dtype=torch.float64),
+                                generator=g).clamp(1, n).to(torch.int64)
+    else:
+        lengths = torch.full((m,), int(L), device=device, dtype=torch.int64)
+    Lmax = int(lengths.max().item())
+    if Lmax > n:
+        raise ValueError("row length exceeds n")
+    cols = torch.randint(0, n, (m, Lmax), generator=g, device=device, dtype=torch.int64)
+    srt = torch.sort(cols, dim=1)[0]
     for _ in range(1000):
-        bad = (cols[:, 1:] == cols[:, :-1]).any(dim=1).nonzero().flatten()
+        bad = (srt[:, 1:] == srt[:, :-1]).any(dim=1).nonzero().flatten()
         if bad.numel() == 0:
             break
-        redo = torch.randint(0, n, (bad.numel(), L), generator=g, device=device, dtype=torch.int64)
-        cols[bad] = torch.sort(redo, dim=1)[0]
+        cols[bad] = torch.randint(0, n, (bad.numel(), Lmax), generator=g, device=device,
+                                  dtype=torch.int64)
+        srt[bad] = torch.sort(cols[bad], dim=1)[0]
     else:
         raise RuntimeError("could not draw distinct columns")
-    v = torch.randn((m, L), generator=g, device=device, dtype=torch.float64)
+    # each row keeps its first L_i draws (a uniform subset), ascending; the rest
+    # become a sentinel that sorts last
+    keep = torch.arange(Lmax, device=device)[None, :] < lengths[:, None]
+    cols = torch.where(keep, cols, torch.full_like(cols, n))
+    cols, order = torch.sort(cols, dim=1)
+    keep = cols < n
+    v = torch.randn((m, Lmax), generator=g, device=device, dtype=torch.float64) * keep
     scale = 1.0 / torch.sqrt((v * v).sum(dim=1, keepdim=True))
     if row_norms == "lognormal":
         scale = scale * torch.exp(torch.randn((m, 1), generator=g, device=device,
@@ -269,8 +290,9 @@ def make_system_torch(m: int, n: int, L: int, seed: int, *, row_norms: str = "un
         v64 = store32.to(torch.float64)
         store = store32.view(torch.int16)
     x_true = torch.randn(n, generator=g, device=device, dtype=torch.float64)
-    b = (v64 * x_true[cols]).sum(dim=1)
-    row_ptr = torch.arange(0, (m + 1) * L, L, device=device, dtype=torch.int64)
-    return {"m": m, "n": n, "L": L, "row_ptr": row_ptr, "col": cols.to(torch.int32).reshape(-1),
-            "val_store": store.reshape(-1).contiguous(), "x_true": x_true, "b": b,
+    b = (v64 * x_true[cols.clamp(max=n - 1)]).sum(dim=1)
+    row_ptr = torch.zeros(m + 1, device=device, dtype=torch.int64)
+    row_ptr[1:] = torch.cumsum(lengths, 0)
+    return {"m": m, "n": n, "L": L, "row_ptr": row_ptr, "col": cols[keep].to(torch.int32),
+            "val_store": store[keep].contiguous(), "x_true": x_true, "b": b,
             "value_dtype": value_dtype, "seed": int(seed)}

@@ -88,10 +88,10 @@ def test_sequential_iterate_matches_oracle_plain_f64_workload():
         assert abs(info.rel_err - res.rel_err) <= 1e-3 * res.rel_err
 
 
-@pytest.mark.parametrize("subwarp", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("subwarp", [1, 2, 4, 8, 16, 32])
 def test_sequential_iterate_ragged_rows_every_subwarp(subwarp):
     # row lengths 1..70: unaligned starts (padding path), chunk tails, rows
-    # longer than 4*subwarp*2 entries (re-load path)
+    # longer than 4*subwarp*2 entries (re-load path); subwarp 1 = one lane per row
     s = synth.make_system(700, 400, (1, 70), 4242, row_norms="lognormal", value_dtype="f64")
     seed = synth.solver_seed(s.seed)
     with asyrk.Problem.from_system(s) as p:

@@ -1,0 +1,97 @@
+"""Table 2's workloads on the GPU: Section 5's generator (delta*m*n nonzeros at
+random positions, so Poisson row lengths; unit rows), m < n, and the stopping
+measure ||A^T(Ax - b)||^2 <= 1e-5 (absolute).
+
+  * the GPU's FP64 ||A^T(Ax-b)||^2 equals the oracle's;
+  * a solve that stops on that measure meets it (re-measured on the host in
+    FP64) within 1.5x the oracle's sweep count to the same threshold;
+  * from x0 = 0 the result is the minimum-norm solution pinv(A) b, as for the
+    sequential method;
+  * the first Table 2 shape at full size (m=80000, n=100000, delta=0.001)
+    reaches the threshold, checked on the host.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_4780_gb300 import asyrk, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    asyrk.load()
+
+
+def _normal2(s, x):
+    g = oracle.normal_residual(s.m, s.n, s.row_ptr, s.col, s.val64, s.b, x)
+    return float(g @ g)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_normal_residual_matches_oracle(dtype):
+    s = synth.make_system(3000, 4000, ("poisson", 20), 31, row_norms="unit", value_dtype=dtype)
+    x = np.random.default_rng(2).standard_normal(s.n)
+    with asyrk.Problem.from_system(s) as p:
+        got = p.normal_residual(x)
+    want = _normal2(s, x)
+    assert abs(got - want) <= 1e-12 * want
+
+
+def _oracle_sweeps_to_normal(s, tol, seed, max_sweeps=400):
+    samp = oracle.Sampler(s.m, s.row_ptr, s.val64)
+    x = np.zeros(s.n)
+    for k in range(1, max_sweeps + 1):
+        oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, s.val64, s.b, x, 1.0, seed, 0, (k - 1) * s.m,
+                        s.m, sampler=samp)
+        if _normal2(s, x) <= tol:
+            return k
+    raise AssertionError("oracle did not reach the threshold")
+
+
+def test_solve_stops_on_table2_measure_within_oracle_sweeps():
+    s = synth.make_system(8000, 10000, ("poisson", 10), 41, row_norms="unit", value_dtype="f32")
+    seed = synth.solver_seed(s.seed)
+    med = np.median([_oracle_sweeps_to_normal(s, 1e-5, seed + k) for k in range(3)])
+    with asyrk.Problem.from_system(s) as p:
+        x = np.zeros(s.n)
+        st, info = p.solve(x, tol=1e-5, max_sweeps=400, measure=asyrk.MEASURE_NORMAL_RESIDUAL)
+        assert st == asyrk.OK, info.as_dict()
+        assert info.sweeps <= 1.5 * med, (info.sweeps, med)
+    assert _normal2(s, x) <= 1e-5
+
+
+def test_underdetermined_limit_is_the_minimum_norm_solution():
+    s = synth.make_system(800, 1000, ("poisson", 12), 43, row_norms="unit", value_dtype="f64")
+    A = oracle.dense(s.m, s.n, s.row_ptr, s.col, s.val64)
+    x_mn = np.linalg.pinv(A) @ s.b
+    with asyrk.Problem.from_system(s) as p:
+        x = np.zeros(s.n)
+        st, info = p.solve(x, tol=1e-24, max_sweeps=3000, measure=asyrk.MEASURE_NORMAL_RESIDUAL)
+        assert st in (asyrk.OK, asyrk.NOT_CONVERGED)
+    assert np.linalg.norm(x - x_mn) <= 1e-9 * np.linalg.norm(x_mn)
+
+
+def test_first_table2_shape_full_size():
+    import torch
+    d = synth.make_system_torch(80000, 100000, ("poisson", 100), 777, row_norms="unit",
+                                value_dtype="f32")
+    torch.cuda.synchronize()
+    with asyrk.Problem(80000, 100000, d["row_ptr"], d["col"], d["val_store"], asyrk.F32, d["b"],
+                       seed=5, device_ptrs=True) as p:
+        x = torch.zeros(100000, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        st, info = p.solve(x, tol=1e-5, max_sweeps=2000, device_ptrs=True,
+                           measure=asyrk.MEASURE_NORMAL_RESIDUAL)
+        assert st == asyrk.OK, info.as_dict()
+    # host FP64 re-measure of ||A^T(Ax - b)||^2 from the generated arrays
+    rp = d["row_ptr"].cpu().numpy()
+    col = d["col"].cpu().numpy()
+    val = d["val_store"].cpu().numpy().astype(np.float64)
+    b = d["b"].cpu().numpy()
+    g = oracle.normal_residual(80000, 100000, rp, col, val, b, x.cpu().numpy())
+    assert float(g @ g) <= 1e-5

@@ -219,3 +219,18 @@ def test_problem_checks(defect):
     elif defect == "b_inf":
         b[2] = np.inf
     assert oracle.validate(m, n, row_ptr, col, val, b) == oracle.EINVAL
+
+
+def test_underdetermined_system_converges_to_the_minimum_norm_solution():
+    # m < n: the solutions form an affine set; every RK step moves x along a row
+    # of A, so from x0 = 0 the iterates stay in range(A^T) and the limit is the
+    # projection of 0 onto the solution set, pinv(A) b (a closed form)
+    s = synth.make_system(120, 300, ("poisson", 6), 17, row_norms="unit", value_dtype="f64")
+    A = oracle.dense(s.m, s.n, s.row_ptr, s.col, s.val64)
+    x_mn = np.linalg.pinv(A) @ s.b
+    x = np.zeros(s.n)
+    oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, s.val64, s.b, x, 1.0, 3, 0, 0, 600 * s.m)
+    assert np.linalg.norm(x - x_mn) <= 1e-10 * np.linalg.norm(x_mn)
+    assert np.linalg.norm(x - s.x_true) > 1e-2 * np.linalg.norm(s.x_true)  # x* is not the limit
+    g = oracle.normal_residual(s.m, s.n, s.row_ptr, s.col, s.val64, s.b, x)
+    assert float(g @ g) < 1e-18
