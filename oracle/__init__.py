@@ -16,6 +16,8 @@ Paper passages followed (section / equation):
   * the projection: Eq. (2), with a step-length factor gamma;
   * full-row update, single thread equals the usual RK: Section 5;
   * the expected one-step decrease and the rate 1 - lambda_min/||A||_F^2: Eq. (3);
+  * sampling without replacement, reshuffled each scan (the paper's
+    implementation, Section 5) and the single-coordinate update (Algorithm 1);
   * lambda_min, lambda_max, mu, nu: Section 1, "Notation and Assumption".
 """
 from __future__ import annotations
@@ -33,6 +35,9 @@ _SRC = os.path.join(_HERE, "asyrk_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
+
+SAMPLE_WEIGHTED, SAMPLE_SHUFFLED = 0, 1
+UPDATE_ROW, UPDATE_SINGLE = 0, 1
 
 OK = 0
 EINVAL = -1
@@ -83,6 +88,17 @@ def _bind(path):
     lib.oracle_rk_solve.argtypes = [i64, i64, P, P, P, P, P, f64, u64, u32, u64, f64,
                                     i64, i64, P, ctypes.POINTER(OracleResult)]
     lib.oracle_rk_solve.restype = ctypes.c_int
+    lib.oracle_shuffle.argtypes = [u64, u32, u64, i64, i64]
+    lib.oracle_shuffle.restype = i64
+    lib.oracle_draw_rows_ex.argtypes = [u64, u32, u64, i64, i64, P, P, ctypes.c_int, ctypes.c_int,
+                                        P]
+    lib.oracle_draw_rows_ex.restype = None
+    lib.oracle_rk_steps_ex.argtypes = [i64, P, P, P, P, P, P, P, ctypes.c_int, u64, u32, f64, u64,
+                                       i64, P, i64, P, P, P, P, ctypes.c_int, ctypes.c_int]
+    lib.oracle_rk_steps_ex.restype = None
+    lib.oracle_rk_solve_ex.argtypes = [i64, i64, P, P, P, P, P, f64, u64, u32, u64, f64, i64, i64,
+                                       P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(OracleResult)]
+    lib.oracle_rk_solve_ex.restype = ctypes.c_int
     return lib
 
 
@@ -154,13 +170,19 @@ def alias_table(w, F):
     return thr, alias, int(u)
 
 
-def draw_rows(seed, stream, j0, count, thr, alias, uniform):
-    """Rows i(j) for j = j0 .. j0+count-1 of the Philox/alias row sequence."""
+def draw_rows(seed, stream, j0, count, thr, alias, uniform, sampling=SAMPLE_WEIGHTED):
+    """Rows i(j) for j = j0 .. j0+count-1 of the row sequence (Philox/alias, or
+    shuffled sweeps)."""
     m = thr.shape[0]
     out = np.zeros(count, dtype=np.int32)
-    _load().oracle_draw_rows(seed, stream, j0, count, m, _p(thr), _p(alias), int(uniform),
-                             _p(out))
+    _load().oracle_draw_rows_ex(seed, stream, j0, count, m, _p(thr), _p(alias), int(uniform),
+                                int(sampling), _p(out))
     return out
+
+
+def shuffle(seed, stream, k, m, q):
+    """pi_k(q): position q of sweep k in the shuffled order of rows 0..m-1."""
+    return int(_load().oracle_shuffle(seed, stream, k, m, q))
 
 
 # --------------------------------------------------------------------------
@@ -205,7 +227,7 @@ class Sampler:
 
 
 def rk_steps(m, n, row_ptr, col, val, b, x, gamma, seed, stream, j0, nsteps,
-             sampler=None, x_true=None, trace=False):
+             sampler=None, x_true=None, trace=False, sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW):
     """Apply steps j0..j0+nsteps-1 of Eq. (2) (step length gamma) to x in place.
 
     With ``trace`` returns (rows, r, err2): the row of each step, its residual
@@ -219,23 +241,24 @@ def rk_steps(m, n, row_ptr, col, val, b, x, gamma, seed, stream, j0, nsteps,
     rows = np.zeros(nsteps, dtype=np.int32) if trace else None
     rr = np.zeros(nsteps, dtype=np.float64) if trace else None
     e2 = np.zeros(nsteps, dtype=np.float64) if (trace and xt is not None) else None
-    _load().oracle_rk_steps(m, _p(rp), _p(c), _p(v), _p(bb), _p(s.w), _p(s.thr), _p(s.alias),
-                            int(s.uniform), seed, stream, float(gamma), j0, nsteps, _p(x), n,
-                            _p(xt), _p(rows), _p(rr), _p(e2))
+    _load().oracle_rk_steps_ex(m, _p(rp), _p(c), _p(v), _p(bb), _p(s.w), _p(s.thr), _p(s.alias),
+                               int(s.uniform), seed, stream, float(gamma), j0, nsteps, _p(x), n,
+                               _p(xt), _p(rows), _p(rr), _p(e2), int(sampling), int(update))
     return (rows, rr, e2) if trace else None
 
 
 def rk_solve(m, n, row_ptr, col, val, b, x, gamma, seed, tol, max_sweeps,
-             check_every=1, x_true=None, stream=0, j0=0):
+             check_every=1, x_true=None, stream=0, j0=0, sampling=SAMPLE_WEIGHTED,
+             update=UPDATE_ROW):
     """Sequential RK to tolerance; x is updated in place.  Returns OracleResult."""
     rp, c, v = _csr(row_ptr, col, val)
     bb = np.ascontiguousarray(b, dtype=np.float64)
     assert x.dtype == np.float64 and x.flags.c_contiguous
     xt = None if x_true is None else np.ascontiguousarray(x_true, dtype=np.float64)
     res = OracleResult()
-    _load().oracle_rk_solve(m, n, _p(rp), _p(c), _p(v), _p(bb), _p(x), float(gamma), seed,
-                            stream, j0, float(tol), max_sweeps, check_every, _p(xt),
-                            ctypes.byref(res))
+    _load().oracle_rk_solve_ex(m, n, _p(rp), _p(c), _p(v), _p(bb), _p(x), float(gamma), seed,
+                               stream, j0, float(tol), max_sweeps, check_every, _p(xt),
+                               int(sampling), int(update), ctypes.byref(res))
     return res
 
 

@@ -36,6 +36,23 @@
  *   - every entry left in either stack gets thr = 2^32 - 1, alias = itself;
  *   - if all w_i are bit-identical, the table is skipped and i = bucket.
  *
+ * Shuffled sweeps (the paper's implementation visits rows without
+ * replacement, reshuffled after each scan, Section 5): projection j belongs to
+ * sweep k = floor(j/m) at position q = j mod m and uses row pi_k(q), where
+ * pi_k is a bijection of [0, m): a 4-round balanced Feistel network on 2h bits
+ * (h = max(1, ceil(log2(m)/2))) iterated until the value falls below m (cycle
+ * walking; after 4096 steps, which does not happen in practice, q itself).
+ * Round r maps (L, R) to (R, L xor (F(R xor K_r) and (2^h - 1))) with F
+ * MurmurHash3's 32-bit finalizer (Appleby) and K_0..K_3 the four Philox words
+ * at counter (k_lo, k_hi, stream, 1).
+ *
+ * Single-coordinate update (Algorithm 1): instead of the whole row, only the
+ * entry t of supp(a_i) is updated, x_t <- x_t - gamma theta_i A_it r/||a_i||^2,
+ * theta_i = ||a_i||_0, t = floor(u2 theta_i / 2^32) with u2 the third Philox
+ * word of projection j (counter (j_lo, j_hi, stream, 0)).  With unit rows this
+ * is Algorithm 1's step; its expectation over t is the full-row step (the
+ * identity E_t[theta P_t a] = a used in the proof of Theorem 1).
+ *
  * Arithmetic is round-to-nearest FP64 in the order written, with no FMA
  * contraction (the build passes -ffp-contract=off): w_i sums val^2 in CSR
  * order, F sums w_i in index order, a_i^T x sums in CSR order.
@@ -183,6 +200,66 @@ void oracle_draw_rows(uint64_t seed, uint32_t stream, uint64_t j0, int64_t count
                                            alias, uniform);
 }
 
+/* MurmurHash3's 32-bit finalizer (Appleby): an avalanche mix of 32 bits. */
+static uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+/* pi_k(q): position q of sweep k in the shuffled order of rows 0..m-1. */
+int64_t oracle_shuffle(uint64_t seed, uint32_t stream, uint64_t k, int64_t m, int64_t q)
+{
+    int bits = 0;
+    while (((int64_t)1 << bits) < m) ++bits;
+    int h = (bits + 1) / 2;
+    if (h < 1) h = 1;
+    const uint64_t mask = ((uint64_t)1 << h) - 1;
+    uint32_t ctr[4] = {(uint32_t)k, (uint32_t)(k >> 32), stream, 1u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t K[4];
+    oracle_philox4x32_10(ctr, key, K);
+    uint64_t v = (uint64_t)q;
+    for (int walk = 0; walk < 4096; ++walk) {
+        uint64_t L = v >> h, R = v & mask;
+        for (int r = 0; r < 4; ++r) {
+            uint64_t nl = R;
+            uint64_t nr = L ^ ((uint64_t)fmix32((uint32_t)R ^ K[r]) & mask);
+            L = nl;
+            R = nr;
+        }
+        v = (L << h) | R;
+        if ((int64_t)v < m) return (int64_t)v;
+    }
+    return q;
+}
+
+/* row of projection j under a sampling scheme: 0 = weighted i.i.d. (alias),
+ * 1 = shuffled sweeps */
+int64_t oracle_draw_row_ex(uint64_t seed, uint32_t stream, uint64_t j, int64_t m,
+                           const uint32_t *thr, const uint32_t *alias, int uniform,
+                           int sampling)
+{
+    if (sampling == 1) {
+        const uint64_t k = j / (uint64_t)m;
+        return oracle_shuffle(seed, stream, k, m, (int64_t)(j - k * (uint64_t)m));
+    }
+    return oracle_draw_row(seed, stream, j, m, thr, alias, uniform);
+}
+
+void oracle_draw_rows_ex(uint64_t seed, uint32_t stream, uint64_t j0, int64_t count, int64_t m,
+                         const uint32_t *thr, const uint32_t *alias, int uniform, int sampling,
+                         int32_t *rows)
+{
+    for (int64_t t = 0; t < count; ++t)
+        rows[t] = (int32_t)oracle_draw_row_ex(seed, stream, j0 + (uint64_t)t, m, thr, alias,
+                                              uniform, sampling);
+}
+
 /* ------------------------------------------------------------------ */
 /* Error measures.                                                      */
 /* ------------------------------------------------------------------ */
@@ -234,21 +311,24 @@ static double err_norm(int64_t n, const double *x, const double *xs)
 }
 
 /* ------------------------------------------------------------------ */
-/* The RK iteration, Eq. (2) with step-length gamma, full-row update,   */
-/* steps j = j0 .. j0+nsteps-1 of the row sequence.  When trace arrays  */
+/* The RK iteration, Eq. (2) with step-length gamma, steps j = j0 ..    */
+/* j0+nsteps-1 of the row sequence; update 0 = the full row (Section 5),*/
+/* 1 = one coordinate (Algorithm 1, see the header).  When trace arrays  */
 /* are given, step t records the row, the residual r = a_i^T x - b_i    */
 /* before the step and, with x_true, ||x_j - x*||^2 before the step.    */
 /* w must hold ||a_i||^2 (oracle_row_weights).                          */
 /* ------------------------------------------------------------------ */
-void oracle_rk_steps(int64_t m, const int64_t *row_ptr, const int32_t *col,
-                     const double *val, const double *b, const double *w,
-                     const uint32_t *thr, const uint32_t *alias, int uniform,
-                     uint64_t seed, uint32_t stream, double gamma, uint64_t j0,
-                     int64_t nsteps, double *x, int64_t n, const double *x_true,
-                     int32_t *trace_row, double *trace_r, double *trace_err2)
+void oracle_rk_steps_ex(int64_t m, const int64_t *row_ptr, const int32_t *col,
+                        const double *val, const double *b, const double *w,
+                        const uint32_t *thr, const uint32_t *alias, int uniform,
+                        uint64_t seed, uint32_t stream, double gamma, uint64_t j0,
+                        int64_t nsteps, double *x, int64_t n, const double *x_true,
+                        int32_t *trace_row, double *trace_r, double *trace_err2,
+                        int sampling, int update)
 {
     for (int64_t t = 0; t < nsteps; ++t) {
-        int64_t i = oracle_draw_row(seed, stream, j0 + (uint64_t)t, m, thr, alias, uniform);
+        const uint64_t j = j0 + (uint64_t)t;
+        int64_t i = oracle_draw_row_ex(seed, stream, j, m, thr, alias, uniform, sampling);
         double dot = 0.0;
         for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) dot += val[k] * x[col[k]];
         double r = dot - b[i];
@@ -259,8 +339,30 @@ void oracle_rk_steps(int64_t m, const int64_t *row_ptr, const int32_t *col,
             trace_err2[t] = e * e;
         }
         double s = gamma * r / w[i];
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) x[col[k]] -= s * val[k];
+        if (update == 1) {
+            uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(j >> 32), stream, 0u};
+            uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+            uint32_t u[4];
+            oracle_philox4x32_10(ctr, key, u);
+            const int64_t theta = row_ptr[i + 1] - row_ptr[i];
+            const int64_t pick = (int64_t)(((uint64_t)u[2] * (uint64_t)theta) >> 32);
+            const int64_t k = row_ptr[i] + pick;
+            x[col[k]] -= ((double)theta * s) * val[k];
+        } else {
+            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) x[col[k]] -= s * val[k];
+        }
     }
+}
+
+void oracle_rk_steps(int64_t m, const int64_t *row_ptr, const int32_t *col,
+                     const double *val, const double *b, const double *w,
+                     const uint32_t *thr, const uint32_t *alias, int uniform,
+                     uint64_t seed, uint32_t stream, double gamma, uint64_t j0,
+                     int64_t nsteps, double *x, int64_t n, const double *x_true,
+                     int32_t *trace_row, double *trace_r, double *trace_err2)
+{
+    oracle_rk_steps_ex(m, row_ptr, col, val, b, w, thr, alias, uniform, seed, stream, gamma, j0,
+                       nsteps, x, n, x_true, trace_row, trace_r, trace_err2, 0, 0);
 }
 
 typedef struct oracle_result {
@@ -277,11 +379,11 @@ typedef struct oracle_result {
  * when it is <= tol, or after max_sweeps sweeps (NOT_CONVERGED), or when the
  * measure is not finite or has grown by 1e30 (DIVERGED).  Steps are counted
  * from j = j0. */
-int oracle_rk_solve(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
-                    const double *val, const double *b, double *x, double gamma,
-                    uint64_t seed, uint32_t stream, uint64_t j0, double tol,
-                    int64_t max_sweeps, int64_t check_every, const double *x_true,
-                    oracle_result *res)
+int oracle_rk_solve_ex(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                       const double *val, const double *b, double *x, double gamma,
+                       uint64_t seed, uint32_t stream, uint64_t j0, double tol,
+                       int64_t max_sweeps, int64_t check_every, const double *x_true,
+                       int sampling, int update, oracle_result *res)
 {
     memset(res, 0, sizeof(*res));
     res->rel_err = -1.0;
@@ -319,8 +421,8 @@ int oracle_rk_solve(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t 
     while (status == OR_NOT_CONVERGED && sweeps < max_sweeps) {
         int64_t k = check_every;
         if (k > max_sweeps - sweeps) k = max_sweeps - sweeps;
-        oracle_rk_steps(m, row_ptr, col, val, b, w, thr, alias, uniform, seed, stream,
-                        gamma, j, k * m, x, n, NULL, NULL, NULL, NULL);
+        oracle_rk_steps_ex(m, row_ptr, col, val, b, w, thr, alias, uniform, seed, stream,
+                           gamma, j, k * m, x, n, NULL, NULL, NULL, NULL, sampling, update);
         j += (uint64_t)(k * m);
         sweeps += k;
         meas = x_true ? err_norm(n, x, x_true) / ref
@@ -342,4 +444,14 @@ int oracle_rk_solve(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t 
     res->status = status;
     free(w); free(thr); free(alias);
     return status;
+}
+
+int oracle_rk_solve(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                    const double *val, const double *b, double *x, double gamma,
+                    uint64_t seed, uint32_t stream, uint64_t j0, double tol,
+                    int64_t max_sweeps, int64_t check_every, const double *x_true,
+                    oracle_result *res)
+{
+    return oracle_rk_solve_ex(m, n, row_ptr, col, val, b, x, gamma, seed, stream, j0, tol,
+                              max_sweeps, check_every, x_true, 0, 0, res);
 }

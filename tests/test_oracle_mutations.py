@@ -79,6 +79,44 @@ def pin_solver_reaches_tolerance():
     return res.status == oracle.OK and err <= 1e-8
 
 
+def pin_shuffle_is_permutation():
+    m = 1000
+    w = np.ones(m)
+    thr, alias, uniform = oracle.alias_table(w, float(m))
+    rows = oracle.draw_rows(5, 0, 0, m, thr, alias, uniform, sampling=oracle.SAMPLE_SHUFFLED)
+    return np.array_equal(np.sort(rows), np.arange(m))
+
+
+def pin_single_coordinate_expectation():
+    s = synth.make_system(24, 10, (2, 5), 5, row_norms="lognormal", value_dtype="f64")
+    samp = oracle.Sampler(s.m, s.row_ptr, s.val64)
+    x0 = s.x_true + np.random.default_rng(1).standard_normal(s.n)
+    seed, gamma = 21, 0.3
+    where = {}
+    rows = oracle.draw_rows(seed, 0, 0, 3_000_000, samp.thr, samp.alias, samp.uniform)
+    for j in range(rows.size):
+        i = int(rows[j])
+        theta = int(s.row_ptr[i + 1] - s.row_ptr[i])
+        u = oracle.philox4x32_10([j & 0xFFFFFFFF, j >> 32, 0, 0], [seed, 0])
+        where.setdefault((i, (int(u[2]) * theta) >> 32), j)
+        if len(where) == s.nnz:
+            break
+    expect = 0.0
+    for (i, t), j in where.items():
+        theta = int(s.row_ptr[i + 1] - s.row_ptr[i])
+        x = x0.copy()
+        oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, s.val64, s.b, x, gamma, seed, 0, j, 1,
+                        sampler=samp, update=oracle.UPDATE_SINGLE)
+        d = x - s.x_true
+        expect += samp.w[i] / samp.F / theta * float(d @ d)
+    A = oracle.dense(s.m, s.n, s.row_ptr, s.col, s.val64)
+    e = x0 - s.x_true
+    r = A @ e
+    th = np.diff(s.row_ptr)
+    exact = float(e @ e) - 2 * gamma / samp.F * float(r @ r) + gamma**2 / samp.F * float(th @ (r * r))
+    return abs(expect - exact) <= 1e-12 * float(e @ e)
+
+
 MUTATIONS = [
     ("dropped gamma", "double s = gamma * r / w[i];", "double s = r / w[i];", pin_step_identity),
     ("sign of b", "double r = dot - b[i];", "double r = dot + b[i];", pin_step_identity),
@@ -102,6 +140,15 @@ MUTATIONS = [
     ("Philox key schedule", "k1 += PHILOX_W1;", "k1 += PHILOX_W0;", pin_philox_counter_words),
     ("Philox word swap", "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi1 ^ c3 ^ k0;",
      pin_philox_counter_words),
+    ("single update without theta", "x[col[k]] -= ((double)theta * s) * val[k];",
+     "x[col[k]] -= s * val[k];", pin_single_coordinate_expectation),
+    ("single update picks the wrong entry",
+     "const int64_t k = row_ptr[i] + pick;", "const int64_t k = row_ptr[i];",
+     pin_single_coordinate_expectation),
+    ("Feistel round not a permutation",
+     "uint64_t nr = L ^ ((uint64_t)fmix32((uint32_t)R ^ K[r]) & mask);",
+     "uint64_t nr = R ^ ((uint64_t)fmix32((uint32_t)L ^ K[r]) & mask);",
+     pin_shuffle_is_permutation),
     ("stop test on wrong measure", "if (meas <= tol) status = OR_OK;\n    }",
      "if (meas <= 1e3 * tol) status = OR_OK;\n    }", pin_solver_reaches_tolerance),
 ]
