@@ -92,6 +92,30 @@ typedef enum asyrk_measure {
     ASYRK_MEASURE_NORMAL_RESIDUAL = 2
 } asyrk_measure;
 
+typedef enum asyrk_sampling {
+    /* rows drawn i.i.d. with probability ||a_i||^2/||A||_F^2 (Section 1;
+     * the analysis of Section 3): Philox and the alias table, as above      */
+    ASYRK_SAMPLE_WEIGHTED = 0,
+    /* every sweep of m projections visits each row once, in a new order per
+     * sweep (the paper's implementation samples without replacement,
+     * reshuffled after each scan, Section 5); row weights are not used.
+     * Projection j of sweep k = j div m, position q = j mod m, uses row
+     * pi_k(q): a 4-round balanced Feistel network on 2h bits (2^(2h) >= m)
+     * walked until it lands below m, round r xoring into the left half the
+     * low h bits of MurmurHash3's 32-bit finalizer of (right half xor K_r),
+     * K_0..K_3 = Philox at counter (k_lo, k_hi, stream, 1)                   */
+    ASYRK_SAMPLE_SHUFFLED = 1
+} asyrk_sampling;
+
+typedef enum asyrk_update {
+    /* all of supp(a_i) (Section 5's implementation; Eq. (2))                */
+    ASYRK_UPDATE_ROW = 0,
+    /* one coordinate t, x_t -= gamma theta_i A_it r / ||a_i||^2, theta_i =
+     * ||a_i||_0, t = floor(u2 theta_i / 2^32) with u2 the third Philox word of
+     * the projection (Algorithm 1; with unit rows exactly its step)         */
+    ASYRK_UPDATE_SINGLE = 1
+} asyrk_update;
+
 typedef struct asyrk_create_opts {
     uint64_t seed;       /* Philox key of the row sequence                       */
     int32_t device_ptrs; /* 1: row_ptr, col_idx, values, b are device pointers  */
@@ -115,7 +139,9 @@ typedef struct asyrk_solve_opts {
                                 updates, where one row may be applied several times
                                 from the same stale x                                 */
     int32_t measure;         /* asyrk_measure of the convergence check               */
-    int32_t reserved2;       /* must be 0                                            */
+    int32_t sampling;        /* asyrk_sampling of the row sequence                   */
+    int32_t update;          /* asyrk_update                                         */
+    int32_t reserved3;       /* must be 0                                            */
 } asyrk_solve_opts;
 
 typedef struct asyrk_solve_info {
@@ -190,10 +216,11 @@ int asyrk_residual(asyrk_problem *p, const double *x, int x_on_device, double *r
 int asyrk_normal_residual(asyrk_problem *p, const double *x, int x_on_device, double *value);
 
 /* The rows drawn by projections j0 .. j0+count-1 with Philox stream id
- * `stream_id`, computed by the GPU sampler that the projection kernels use;
- * rows_out: count int32 on the host.  Errors: EINVAL (count < 0), ECUDA. */
+ * `stream_id` under `sampling` (asyrk_sampling), computed by the GPU sampler
+ * that the projection kernels use; rows_out: count int32 on the host.
+ * Errors: EINVAL (count < 0, unknown sampling), ECUDA. */
 int asyrk_draw_rows(asyrk_problem *p, uint64_t j0, int64_t count, uint32_t stream_id,
-                    int32_t *rows_out);
+                    int sampling, int32_t *rows_out);
 
 /* Position of the row sequence: the j of the next projection.  Saving it
  * with x and restoring both (asyrk_set_position) resumes a run; in
@@ -244,6 +271,8 @@ typedef struct asyrk_batch_opts {
     void *stream;           /* cudaStream_t; NULL = legacy default stream          */
     int32_t graph;          /* >= 0: one graph launch per solve (default); -1: host loop */
     int32_t row_exclusion;  /* as in asyrk_solve_opts                               */
+    int32_t sampling;       /* asyrk_sampling of every member                       */
+    int32_t update;         /* asyrk_update of every member                         */
 } asyrk_batch_opts;
 
 typedef struct asyrk_batch_info {

@@ -21,6 +21,8 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_CONVERGED, DIVERGED = 0, -1, -2, -3, -4
 ECANCELED = -5
 MODE_SEQUENTIAL, MODE_ASYNC, MODE_REFINE = 0, 1, 2
 MEASURE_AUTO, MEASURE_RESIDUAL, MEASURE_NORMAL_RESIDUAL = 0, 1, 2
+SAMPLE_WEIGHTED, SAMPLE_SHUFFLED = 0, 1
+UPDATE_ROW, UPDATE_SINGLE = 0, 1
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
 
 
@@ -43,7 +45,8 @@ class SolveOpts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("inner_tol", ctypes.c_double),
                 ("inner_sweeps", ctypes.c_int64), ("profile", ctypes.c_int32),
                 ("row_exclusion", ctypes.c_int32), ("measure", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("sampling", ctypes.c_int32), ("update", ctypes.c_int32),
+                ("reserved3", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -105,7 +108,7 @@ def load(path: str = LIB_PATH):
     lib.asyrk_residual.restype = ctypes.c_int
     lib.asyrk_normal_residual.argtypes = [P, P, ctypes.c_int, ctypes.POINTER(f64)]
     lib.asyrk_normal_residual.restype = ctypes.c_int
-    lib.asyrk_draw_rows.argtypes = [P, u64, i64, u32, P]
+    lib.asyrk_draw_rows.argtypes = [P, u64, i64, u32, ctypes.c_int, P]
     lib.asyrk_draw_rows.restype = ctypes.c_int
     lib.asyrk_get_position.argtypes = [P, ctypes.POINTER(u64)]
     lib.asyrk_get_position.restype = ctypes.c_int
@@ -161,7 +164,8 @@ class TuneResult(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("graph", ctypes.c_int32),
-                ("row_exclusion", ctypes.c_int32)]
+                ("row_exclusion", ctypes.c_int32), ("sampling", ctypes.c_int32),
+                ("update", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -267,9 +271,9 @@ def asyrk_normal_residual(h, x, x_on_device=False):
     return st, out.value
 
 
-def asyrk_draw_rows(h, j0, count, stream_id=0):
+def asyrk_draw_rows(h, j0, count, stream_id=0, sampling=SAMPLE_WEIGHTED):
     rows = np.zeros(count, dtype=np.int32)
-    st = load().asyrk_draw_rows(h, j0, count, stream_id, _ptr(rows))
+    st = load().asyrk_draw_rows(h, j0, count, stream_id, sampling, _ptr(rows))
     return st, rows
 
 
@@ -302,10 +306,12 @@ def _ptr_array(items):
     return arr
 
 
-def asyrk_batch_create(handles, stream=None, graph=True, row_exclusion=0):
+def asyrk_batch_create(handles, stream=None, graph=True, row_exclusion=0,
+                       sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW):
     b = ctypes.c_void_p()
     hs = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
-    o = BatchOpts(stream=_stream(stream), graph=0 if graph else -1, row_exclusion=row_exclusion)
+    o = BatchOpts(stream=_stream(stream), graph=0 if graph else -1, row_exclusion=row_exclusion,
+                  sampling=sampling, update=update)
     st = load().asyrk_batch_create(ctypes.byref(b), hs, len(handles), ctypes.byref(o))
     return st, b
 
@@ -392,12 +398,12 @@ def asyrk_problem_get_stats(h):
 # ---------------------------------------------------------------------------
 def solve_opts(mode=MODE_ASYNC, workers=0, subwarp=0, check_every=1, x_true=None, stream=None,
                inner_tol=0.0, inner_sweeps=0, profile=False, device_ptrs=False, row_exclusion=0,
-               measure=MEASURE_AUTO):
+               measure=MEASURE_AUTO, sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW):
     return SolveOpts(mode=mode, device_ptrs=1 if device_ptrs else 0, workers=workers,
                      subwarp=subwarp, check_every=check_every, x_true=_ptr(x_true),
                      stream=_stream(stream), inner_tol=inner_tol, inner_sweeps=inner_sweeps,
                      profile=1 if profile else 0, row_exclusion=row_exclusion, measure=measure,
-                     reserved2=0)
+                     sampling=sampling, update=update, reserved3=0)
 
 
 class Problem:
@@ -459,8 +465,8 @@ class Problem:
             raise AsyrkError(st, "asyrk_normal_residual")
         return r
 
-    def draw_rows(self, j0, count, stream_id=0):
-        st, rows = asyrk_draw_rows(self.h, j0, count, stream_id)
+    def draw_rows(self, j0, count, stream_id=0, sampling=SAMPLE_WEIGHTED):
+        st, rows = asyrk_draw_rows(self.h, j0, count, stream_id, sampling)
         if st != OK:
             raise AsyrkError(st, "asyrk_draw_rows")
         return rows
@@ -486,10 +492,11 @@ class Problem:
 class Batch:
     """Owns one asyrk_batch handle over a list of Problem objects."""
 
-    def __init__(self, problems, stream=None, graph=True, row_exclusion=0):
+    def __init__(self, problems, stream=None, graph=True, row_exclusion=0,
+                 sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW):
         self.problems = list(problems)
         st, b = asyrk_batch_create([p.h for p in self.problems], stream=stream, graph=graph,
-                                   row_exclusion=row_exclusion)
+                                   row_exclusion=row_exclusion, sampling=sampling, update=update)
         if st != OK:
             raise AsyrkError(st, "asyrk_batch_create")
         self.b = b

@@ -115,6 +115,9 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
     if (opts) o = *opts;
     if (o.row_exclusion < -1 || o.row_exclusion > 1)
         return set_error(ASYRK_EINVAL, "row_exclusion must be -1, 0 or 1");
+    if (o.sampling < ASYRK_SAMPLE_WEIGHTED || o.sampling > ASYRK_SAMPLE_SHUFFLED ||
+        o.update < ASYRK_UPDATE_ROW || o.update > ASYRK_UPDATE_SINGLE)
+        return set_error(ASYRK_EINVAL, "unknown sampling or update");
     std::set<asyrk_problem *> seen;
     int dev = -1;
     ASYRK_CK(cudaGetDevice(&dev));
@@ -172,6 +175,9 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
         D.col = p->col;
         D.val = p->val;
         D.b64 = p->b64;
+        D.sampling = o.sampling;
+        D.update = o.update;
+        D.shuf_h = shuffle_half_bits(p->m);
         b->xoff[k + 1] = b->xoff[k] + p->n;
         busy_off[k] = busy_total;
         busy_total += (p->m + 31) / 32;

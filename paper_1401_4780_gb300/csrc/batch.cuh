@@ -70,6 +70,10 @@ struct SysDesc {
     double outer_ref;     // ||x*|| (with x*) or ||b|| for the outer measure
     int max_k;            // sweeps one engine step may run for this slot (>= 1)
     int k;                // sweeps this step (set by plan)
+    int sampling;         // 0: weighted i.i.d. draws, 1: shuffled sweeps
+    int update;           // 0: the whole row, 1: one coordinate (Algorithm 1)
+    int shuf_h;           // half width of the shuffle's Feistel domain
+    int pad2;
 };
 
 constexpr int SLOT_PLAIN = 0;

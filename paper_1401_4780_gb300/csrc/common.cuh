@@ -138,29 +138,79 @@ __device__ __forceinline__ unsigned draw_row(unsigned long long j, unsigned stre
 }
 
 // ---------------------------------------------------------------------------
+// Shuffled sweeps: projection j of sweep k = j div m, position q = j mod m,
+// uses row pi_k(q), a bijection of [0, m): a 4-round balanced Feistel network
+// on 2h bits (2^(2h) >= m, so at most 4m values) walked until it lands below m;
+// round r xors into the left half the low h bits of MurmurHash3's 32-bit
+// finalizer (Appleby) of (right half xor K_r), K_0..K_3 = Philox at counter
+// (k_lo, k_hi, stream, 1).  After 4096 walks (never seen) q maps to itself.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned murmur_fmix32(unsigned h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// half width h of the Feistel domain for m rows
+static inline int shuffle_half_bits(long long m)
+{
+    int bits = 0;
+    while ((1LL << bits) < m) ++bits;
+    const int h = (bits + 1) / 2;
+    return h < 1 ? 1 : h;
+}
+
+__device__ __forceinline__ unsigned shuffled_position(unsigned long long j, unsigned m,
+                                                      unsigned stream, uint2 key, int h)
+{
+    const unsigned long long k = j / m;
+    const unsigned q = (unsigned)(j - k * m);
+    const uint4 K = philox4x32_10(make_uint4((unsigned)k, (unsigned)(k >> 32), stream, 1u), key);
+    const unsigned mask = (h >= 32) ? 0xffffffffu : ((1u << h) - 1u);
+    unsigned v = q;
+    for (int walk = 0; walk < 4096; ++walk) {
+        unsigned L = v >> h, R = v & mask, t;
+        // four rounds, round r keyed by word r of K
+        t = L ^ (murmur_fmix32(R ^ K.x) & mask); L = R; R = t;
+        t = L ^ (murmur_fmix32(R ^ K.y) & mask); L = R; R = t;
+        t = L ^ (murmur_fmix32(R ^ K.z) & mask); L = R; R = t;
+        t = L ^ (murmur_fmix32(R ^ K.w) & mask); L = R; R = t;
+        v = (L << h) | R;
+        if (v < m) return v;
+    }
+    return q;
+}
+
+// ---------------------------------------------------------------------------
 // launchers (defined in project.cu / measure.cu)
 // ---------------------------------------------------------------------------
 struct ProjectLaunch {
-    asyrk_problem *p;
-    void *x;               // float* or double*
-    bool x_f64;
-    double gamma;
-    unsigned long long j0;
-    unsigned long long count;  // projections in this launch
-    unsigned stream_id;
-    int workers;               // concurrent row groups
-    int subwarp;               // lanes per row group
-    bool sequential;           // one group, strictly ordered projections
-    bool exclusive;            // row exclusion (skip rows another worker holds)
-    bool b_from_rec;           // FP32 b from rec (else b64)
-    cudaStream_t stream;
+    asyrk_problem *p = nullptr;
+    void *x = nullptr;              // float* or double*
+    bool x_f64 = false;
+    double gamma = 1.0;
+    unsigned long long j0 = 0;
+    unsigned long long count = 0;   // projections in this launch
+    unsigned stream_id = 0;
+    int workers = 1;                // concurrent row groups
+    int subwarp = 32;               // lanes per row group
+    bool sequential = false;        // one group, strictly ordered projections
+    bool exclusive = true;          // row exclusion (skip rows another worker holds)
+    int sampling = 0;               // 0: weighted i.i.d. draws, 1: shuffled sweeps
+    int update = 0;                 // 0: the whole row, 1: one coordinate (Algorithm 1)
+    bool b_from_rec = true;         // FP32 b from rec (else b64)
+    cudaStream_t stream = nullptr;
 };
 int launch_project(const ProjectLaunch &L);  // counts into L.p->launches
 int project_max_workers(const asyrk_problem *p, bool x_f64, int subwarp, int *max_workers);
 int choose_subwarp(int64_t max_len, int64_t nnz, int64_t m);
 
 int launch_draw_rows(const asyrk_problem *p, unsigned long long j0, int64_t count,
-                     unsigned stream_id, int32_t *rows_dev, cudaStream_t s);
+                     unsigned stream_id, int sampling, int32_t *rows_dev, cudaStream_t s);
 
 // FP64 reductions; each leaves its result(s) in p->red_out[slot...]
 int launch_err2(asyrk_problem *p, const void *x, bool x_f64, const double *xt, int slot,

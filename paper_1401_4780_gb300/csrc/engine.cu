@@ -213,7 +213,7 @@ __device__ __forceinline__ unsigned long long batch_run_g(const ProjArgs &a, int
 }
 
 template <bool EXCL>
-__global__ void __launch_bounds__(256) k_batch_project(SysDesc *d, int count)
+__global__ void __launch_bounds__(256, 3) k_batch_project(SysDesc *d, int count)  // <= 85 registers
 {
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int s = find_slot_warp(d, count, gw);
@@ -236,6 +236,9 @@ __global__ void __launch_bounds__(256) k_batch_project(SysDesc *d, int count)
     a.workers = (long long)D.nwarps * (32 / D.G);
     a.gamma = (double)D.gamma;
     a.bvec = D.bvec;
+    a.sampling = D.sampling;
+    a.shuf_h = D.shuf_h;
+    a.update = D.update;
     a.busy = D.busy;
     a.skipped = nullptr;
     const int rel = gw - D.warp0;

@@ -460,9 +460,10 @@ extern "C" int asyrk_problem_get_stats(asyrk_problem *p, asyrk_problem_stats *st
 }
 
 extern "C" int asyrk_draw_rows(asyrk_problem *p, uint64_t j0, int64_t count, uint32_t stream_id,
-                               int32_t *rows_out)
+                               int sampling, int32_t *rows_out)
 {
-    if (!p || (count > 0 && !rows_out) || count < 0) return set_error(ASYRK_EINVAL, "bad argument");
+    if (!p || (count > 0 && !rows_out) || count < 0 || sampling < 0 || sampling > 1)
+        return set_error(ASYRK_EINVAL, "bad argument");
     if (count == 0) return ASYRK_OK;
     if (count > p->rows_cap) {
         cudaFree(p->rows_buf);
@@ -471,7 +472,7 @@ extern "C" int asyrk_draw_rows(asyrk_problem *p, uint64_t j0, int64_t count, uin
         ASYRK_CK(cudaMalloc((void **)&p->rows_buf, count * sizeof(int32_t)));
         p->rows_cap = count;
     }
-    int st = launch_draw_rows(p, j0, count, stream_id, p->rows_buf, 0);
+    int st = launch_draw_rows(p, j0, count, stream_id, sampling, p->rows_buf, 0);
     if (st != ASYRK_OK) return st;
     ASYRK_CK(cudaMemcpy(rows_out, p->rows_buf, count * sizeof(int32_t), cudaMemcpyDeviceToHost));
     return ASYRK_OK;

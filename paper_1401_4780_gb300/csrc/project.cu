@@ -22,12 +22,17 @@ __global__ void __launch_bounds__(256, 4) k_project(const ProjArgs a)  // <= 64 
 
 __global__ void k_draw_rows(const RowRec *__restrict__ rec, uint2 key, unsigned m, int uniform,
                             unsigned stream_id, unsigned long long j0, long long count,
-                            int32_t *__restrict__ out)
+                            int sampling, int shuf_h, int32_t *__restrict__ out)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
-    RowRec r;
-    out[t] = (int32_t)draw_row(j0 + (unsigned long long)t, stream_id, key, m, uniform, rec, r);
+    const unsigned long long j = j0 + (unsigned long long)t;
+    if (sampling == 1) {
+        out[t] = (int32_t)shuffled_position(j, m, stream_id, key, shuf_h);
+    } else {
+        RowRec r;
+        out[t] = (int32_t)draw_row(j, stream_id, key, m, uniform, rec, r);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -111,6 +116,9 @@ int launch_project(const ProjectLaunch &L)
     a.count = L.count;
     a.gamma = L.gamma;
     a.bvec = nullptr;
+    a.sampling = L.sampling;
+    a.shuf_h = shuffle_half_bits(p->m);
+    a.update = L.update;
     a.busy = p->busy;
     a.skipped = p->skipped;
     if (L.sequential) {
@@ -128,12 +136,13 @@ int launch_project(const ProjectLaunch &L)
 }
 
 int launch_draw_rows(const asyrk_problem *p, unsigned long long j0, int64_t count,
-                     unsigned stream_id, int32_t *rows_dev, cudaStream_t s)
+                     unsigned stream_id, int sampling, int32_t *rows_dev, cudaStream_t s)
 {
     const uint2 key = make_uint2((unsigned)p->seed, (unsigned)(p->seed >> 32));
     const long long blocks = (count + 255) / 256;
     k_draw_rows<<<(unsigned)blocks, 256, 0, s>>>(p->rec, key, (unsigned)p->m, p->uniform,
-                                                   stream_id, j0, count, rows_dev);
+                                                   stream_id, j0, count, sampling,
+                                                   shuffle_half_bits(p->m), rows_dev);
     ASYRK_CK(cudaGetLastError());
     return ASYRK_OK;
 }

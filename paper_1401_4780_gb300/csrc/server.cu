@@ -292,6 +292,9 @@ static bool admit_locked(asyrk_server *sv, Request *r, int k)
     D.inner_tol = sv->inner_tol;
     D.max_inner = sv->max_inner;
     D.max_k = 32;  // short sweeps run several per engine step
+    D.sampling = ASYRK_SAMPLE_WEIGHTED;
+    D.update = ASYRK_UPDATE_ROW;
+    D.shuf_h = shuffle_half_bits(p->m);
     sv->slot_req[k] = r;
     r->slot = k;
     r->t_admit = now_s();

@@ -152,6 +152,8 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
         L.subwarp = G;
         L.sequential = seq;
         L.exclusive = o.row_exclusion >= 0;
+        L.sampling = o.sampling;
+        L.update = o.update;
         L.b_from_rec = !x_f64;
         L.stream = c.s;
         if ((st = project(c, L)) != ASYRK_OK) return st;
@@ -242,6 +244,8 @@ static int solve_refine(SolveCtx &c, double gamma, double tol, int64_t max_sweep
         L.subwarp = G;
         L.sequential = false;
         L.exclusive = o.row_exclusion >= 0;
+        L.sampling = o.sampling;
+        L.update = o.update;
         L.b_from_rec = true;
         L.stream = c.s;
         if ((st = project(c, L)) != ASYRK_OK) return st;
@@ -290,7 +294,11 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
         return set_error(ASYRK_EINVAL, "row_exclusion must be -1, 0 or 1");
     if (o.measure < ASYRK_MEASURE_AUTO || o.measure > ASYRK_MEASURE_NORMAL_RESIDUAL)
         return set_error(ASYRK_EINVAL, "unknown measure %d", o.measure);
-    if (o.reserved2 != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
+    if (o.sampling < ASYRK_SAMPLE_WEIGHTED || o.sampling > ASYRK_SAMPLE_SHUFFLED)
+        return set_error(ASYRK_EINVAL, "unknown sampling %d", o.sampling);
+    if (o.update < ASYRK_UPDATE_ROW || o.update > ASYRK_UPDATE_SINGLE)
+        return set_error(ASYRK_EINVAL, "unknown update %d", o.update);
+    if (o.reserved3 != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
     if (o.mode == ASYRK_MODE_SEQUENTIAL && o.workers > 1)
         return set_error(ASYRK_EINVAL, "SEQUENTIAL mode has one worker");
 

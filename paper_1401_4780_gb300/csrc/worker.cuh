@@ -37,6 +37,9 @@ struct ProjArgs {
     long long workers;
     double gamma;
     const float *bvec;               // FP32 right-hand side replacing rec.b, or nullptr
+    int sampling;                    // 0: weighted i.i.d. draws, 1: shuffled sweeps
+    int shuf_h;                      // half width of the shuffle's Feistel domain
+    int update;                      // 0: the whole row, 1: one coordinate (Algorithm 1)
     unsigned *busy;                  // row-claim bits (row exclusion)
     unsigned long long *skipped;     // projections skipped by row exclusion
 };
@@ -70,6 +73,14 @@ __device__ __forceinline__ void ld_val4(const bf16_t *p, XT (&v)[4])
     v[1] = (XT)__uint_as_float(a.x & 0xffff0000u);
     v[2] = (XT)__uint_as_float(a.y << 16);
     v[3] = (XT)__uint_as_float(a.y & 0xffff0000u);
+}
+
+// one entry (the single-coordinate update)
+__device__ __forceinline__ double ld_val1(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val1(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val1(const bf16_t *p)
+{
+    return __uint_as_float((unsigned)__ldcs(reinterpret_cast<const unsigned short *>(p)) << 16);
 }
 
 // ---- the shared iterate: gathers from L2 (no L1 copy that could go stale
@@ -160,13 +171,24 @@ __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, lon
         bool act = worker && t < a.count;
         long long start = 0;
         int len = 0;
-        unsigned i = 0;
+        unsigned i = 0, pick = 0;
         XT b = 0, scale = 0;
         if (act) {
             RowRec r;
-            i = draw_row(a.j0 + t, a.stream_id, a.key, a.m, a.uniform, a.rec, r);
+            const unsigned long long j = a.j0 + t;
+            if (a.sampling == 1) {
+                i = shuffled_position(j, a.m, a.stream_id, a.key, a.shuf_h);
+                r = load_rec(a.rec + i);
+            } else {
+                i = draw_row(j, a.stream_id, a.key, a.m, a.uniform, a.rec, r);
+            }
             start = r.start;
             len = (int)r.len;
+            if (a.update == 1) {  // the entry of Algorithm 1: u2 of projection j
+                const uint4 u = philox4x32_10(
+                    make_uint4((unsigned)j, (unsigned)(j >> 32), a.stream_id, 0u), a.key);
+                pick = __umulhi(u.z, (unsigned)len);
+            }
             if (F64) {
                 b = (XT)__ldg(a.b64 + i);
                 scale = (XT)__ldg(a.w64 + i);
@@ -210,7 +232,19 @@ __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, lon
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
 
-        if (act) {
+        if (act && a.update == 1) {
+            // one coordinate: x_t -= gamma theta_i A_it r / ||a_i||^2
+            XT s;
+            if (F64) {
+                s = -((gamma * (acc - b)) / scale);
+            } else {
+                s = -(gamma * (acc - b) * scale);
+            }
+            if (sl == 0) {
+                const long long k = start + pick;
+                red_add(x + a.col[k], ((XT)len * s) * (XT)ld_val1(val + k));
+            }
+        } else if (act) {
             XT s;
             if (F64) {
                 s = -((gamma * (acc - b)) / scale);  // the oracle's (gamma r) / ||a_i||^2

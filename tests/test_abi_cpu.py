@@ -46,10 +46,10 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header():
     # sizes implied by the header's field lists (natural alignment, LP64)
     assert ctypes.sizeof(asyrk.CreateOpts) == 24
-    assert ctypes.sizeof(asyrk.SolveOpts) == 72
+    assert ctypes.sizeof(asyrk.SolveOpts) == 80
     assert ctypes.sizeof(asyrk.SolveInfo) == 96
     assert ctypes.sizeof(asyrk.ProblemStats) == 80
-    assert ctypes.sizeof(asyrk.BatchOpts) == 16
+    assert ctypes.sizeof(asyrk.BatchOpts) == 24
     assert ctypes.sizeof(asyrk.BatchInfo) == 56
     assert ctypes.sizeof(asyrk.TuneResult) == 24
     assert ctypes.sizeof(asyrk.ServerOpts) == 32
