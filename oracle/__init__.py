@@ -99,6 +99,8 @@ def _bind(path):
     lib.oracle_rk_solve_ex.argtypes = [i64, i64, P, P, P, P, P, f64, u64, u32, u64, f64, i64, i64,
                                        P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(OracleResult)]
     lib.oracle_rk_solve_ex.restype = ctypes.c_int
+    lib.oracle_lsq_augment.argtypes = [i64, i64, P, P, P, P, f64, f64, P, P, P, P]
+    lib.oracle_lsq_augment.restype = i64
     return lib
 
 
@@ -212,6 +214,25 @@ def normal_residual(m, n, row_ptr, col, val, b, x):
     g = np.zeros(n, dtype=np.float64)
     _load().oracle_normal_residual(m, n, _p(rp), _p(c), _p(v), _p(bb), _p(xx), _p(g))
     return g
+
+
+def lsq_augment(m, n, row_ptr, col, val, b, zeta, phi=1.0):
+    """Section 6's square consistent system for min ||A x - b||.
+
+    Returns (rows, cols, row_ptr, col, val, rhs) of the matrix
+    [[0, phi A^T], [A, -zeta I]] over (x, y), rows of empty columns left out;
+    its solutions have x = zeta x_LS."""
+    rp, c, v = _csr(row_ptr, col, val)
+    bb = np.ascontiguousarray(b, dtype=np.float64)
+    nnz = int(rp[-1])
+    arp = np.zeros(n + m + 1, dtype=np.int64)
+    acol = np.zeros(2 * nnz + m, dtype=np.int32)
+    aval = np.zeros(2 * nnz + m, dtype=np.float64)
+    ab = np.zeros(n + m, dtype=np.float64)
+    rows = _load().oracle_lsq_augment(m, n, _p(rp), _p(c), _p(v), _p(bb), float(zeta), float(phi),
+                                      _p(arp), _p(acol), _p(aval), _p(ab))
+    e = int(arp[rows])
+    return rows, n + m, arp[:rows + 1].copy(), acol[:e].copy(), aval[:e].copy(), ab[:rows].copy()
 
 
 # --------------------------------------------------------------------------

@@ -53,6 +53,10 @@
  * is Algorithm 1's step; its expectation over t is the full-row step (the
  * identity E_t[theta P_t a] = a used in the proof of Theorem 1).
  *
+ * Least squares (Section 6): oracle_lsq_augment writes the square consistent
+ * system [[0, phi A^T], [A, -zeta I]] (x, y) = (phi A^T b, 0) whose x-block
+ * solutions are zeta x_LS; RK on it is the same projection as above.
+ *
  * Arithmetic is round-to-nearest FP64 in the order written, with no FMA
  * contraction (the build passes -ffp-contract=off): w_i sums val^2 in CSR
  * order, F sums w_i in index order, a_i^T x sums in CSR order.
@@ -454,4 +458,68 @@ int oracle_rk_solve(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t 
 {
     return oracle_rk_solve_ex(m, n, row_ptr, col, val, b, x, gamma, seed, stream, j0, tol,
                               max_sweeps, check_every, x_true, 0, 0, res);
+}
+
+/* ------------------------------------------------------------------ */
+/* Section 6: least squares through a square consistent system.        */
+/* ------------------------------------------------------------------ */
+/* The minimiser of ||A x - b|| solves, for any zeta > 0 and phi > 0,
+ *     A x - zeta y = 0,    phi A^T y = phi A^T b,
+ * whose solutions have x = zeta x_LS (and y = A x_LS).  As a CSR matrix over
+ * the unknowns (x, y) of length n + m the rows are, in this order:
+ *   - for each column j of A with at least one nonzero (a column of zeros
+ *     gives the equation 0 = 0, which is left out): the entries
+ *     (n + i, phi A_ij) for i ascending, right side phi * (sum_i A_ij b_i)
+ *     with the sum taken in ascending i;
+ *   - for each row i of A: its entries (j, A_ij) as given, then
+ *     (n + i, -zeta); right side 0.
+ * The caller sizes the outputs for n + m rows and 2 nnz + m entries; the
+ * return value is the number of rows written. */
+int64_t oracle_lsq_augment(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                           const double *val, const double *b, double zeta, double phi,
+                           int64_t *arow_ptr, int32_t *acol, double *aval, double *ab)
+{
+    const int64_t nnz = row_ptr[m];
+    /* A^T in CSR (the CSC of A) by counting: entries of column j in row order */
+    int64_t *cstart = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t *cfill = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    int64_t *trow = (int64_t *)malloc(((size_t)nnz + 1) * sizeof(int64_t));
+    double *tval = (double *)malloc(((size_t)nnz + 1) * sizeof(double));
+    for (int64_t k = 0; k < nnz; ++k) cstart[col[k] + 1] += 1;
+    for (int64_t j = 0; j < n; ++j) cstart[j + 1] += cstart[j];
+    for (int64_t j = 0; j <= n; ++j) cfill[j] = cstart[j];
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            const int64_t p = cfill[col[k]]++;
+            trow[p] = i;
+            tval[p] = val[k];
+        }
+    int64_t r = 0, e = 0;
+    arow_ptr[0] = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (cstart[j + 1] == cstart[j]) continue;
+        double s = 0.0;
+        for (int64_t p = cstart[j]; p < cstart[j + 1]; ++p) {
+            acol[e] = (int32_t)(n + trow[p]);
+            aval[e] = phi * tval[p];
+            ++e;
+            s += tval[p] * b[trow[p]];
+        }
+        ab[r] = phi * s;
+        arow_ptr[++r] = e;
+    }
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            acol[e] = col[k];
+            aval[e] = val[k];
+            ++e;
+        }
+        acol[e] = (int32_t)(n + i);
+        aval[e] = -zeta;
+        ++e;
+        ab[r] = 0.0;
+        arow_ptr[++r] = e;
+    }
+    free(cstart); free(cfill); free(trow); free(tval);
+    return r;
 }

@@ -117,6 +117,34 @@ def pin_single_coordinate_expectation():
     return abs(expect - exact) <= 1e-12 * float(e @ e)
 
 
+def pin_lsq_solution():
+    m, n, phi = 120, 30, 2.0
+    s = synth.make_system(m, n, 6, 9, row_norms="unit", value_dtype="f64")
+    b = s.b + 0.3 * np.random.default_rng(10).standard_normal(m)
+    A = oracle.dense(m, n, s.row_ptr, s.col, s.val64)
+    x_ls = np.linalg.lstsq(A, b, rcond=None)[0]
+    zeta = np.linalg.svd(A, compute_uv=False).min() / np.sqrt(2)
+    rows, cols, rp, col, val, rhs = oracle.lsq_augment(m, n, s.row_ptr, s.col, s.val64, b, zeta,
+                                                       phi)
+    z = np.zeros(cols)
+    oracle.rk_steps(rows, cols, rp, col, val, rhs, z, 1.0, 3, 0, 0, 3000 * rows)
+    return np.max(np.abs(z[:n] / zeta - x_ls)) <= 1e-8 * np.abs(x_ls).max()
+
+
+def pin_lsq_spectrum():
+    m, n, zeta, phi = 40, 12, 0.2, 2.5
+    s = synth.make_system(m, n, 5, 3, row_norms="lognormal", value_dtype="f64")
+    rows, cols, rp, col, val, rhs = oracle.lsq_augment(m, n, s.row_ptr, s.col, s.val64, s.b, zeta,
+                                                       phi)
+    got = np.sort(np.linalg.svd(oracle.dense(rows, cols, rp, col, val), compute_uv=False))
+    sv = np.linalg.svd(oracle.dense(m, n, s.row_ptr, s.col, s.val64), compute_uv=False)
+    want = []
+    for x in sv:
+        want.extend(np.linalg.svd(np.array([[0.0, phi * x], [x, -zeta]]), compute_uv=False))
+    want = np.sort(np.array(want + [zeta] * (m - sv.size) + [0.0] * (n - sv.size)))
+    return got.shape == want.shape and np.allclose(got, want, rtol=1e-12, atol=1e-12 * want.max())
+
+
 MUTATIONS = [
     ("dropped gamma", "double s = gamma * r / w[i];", "double s = r / w[i];", pin_step_identity),
     ("sign of b", "double r = dot - b[i];", "double r = dot + b[i];", pin_step_identity),
@@ -149,6 +177,13 @@ MUTATIONS = [
      "uint64_t nr = L ^ ((uint64_t)fmix32((uint32_t)R ^ K[r]) & mask);",
      "uint64_t nr = R ^ ((uint64_t)fmix32((uint32_t)L ^ K[r]) & mask);",
      pin_shuffle_is_permutation),
+    ("least squares: sign of zeta", "aval[e] = -zeta;", "aval[e] = zeta;", pin_lsq_solution),
+    ("least squares: right side without phi", "ab[r] = phi * s;", "ab[r] = s;",
+     pin_lsq_solution),
+    ("least squares: A^T block without phi", "aval[e] = phi * tval[p];", "aval[e] = tval[p];",
+     pin_lsq_spectrum),
+    ("least squares: right side over the wrong b",
+     "s += tval[p] * b[trow[p]];", "s += tval[p] * b[p - cstart[j]];", pin_lsq_solution),
     ("stop test on wrong measure", "if (meas <= tol) status = OR_OK;\n    }",
      "if (meas <= 1e3 * tol) status = OR_OK;\n    }", pin_solver_reaches_tolerance),
 ]
