@@ -377,6 +377,48 @@ int asyrk_server_get_stats(asyrk_server *s, asyrk_server_stats *stats);
  * ticket is forgotten. */
 void asyrk_server_destroy(asyrk_server *s);
 
+/* ---- least squares (Section 6) ------------------------------------------
+ * min ||A x - b|| for a possibly inconsistent A x = b is reached by the method
+ * run on the square consistent system
+ *     [ 0   phi A^T ] [x]   [phi A^T b]
+ *     [ A   -zeta I ] [y] = [    0    ]
+ * over z = (x, y) of length n + m, whose solutions have x = zeta x_LS and
+ * y = A x_LS (from z0 = 0 the method reaches the minimum-norm one, so
+ * x = zeta pinv(A) b).  Section 6 shows that phi = 1, zeta = sigma_r/sqrt(2)
+ * (sigma_r the smallest nonzero singular value of A, rows of A normalised)
+ * maximises lambda_min/||.||_F^2 of the system, the quantity the rate of
+ * Theorem 2 depends on. */
+typedef struct asyrk_lsq_opts {
+    double zeta;         /* > 0, finite: the y-block scale                        */
+    double phi;          /* > 0: the A^T-block scale; 0 means 1                   */
+    uint64_t seed;       /* Philox key of the system's row sequence               */
+    int32_t device_ptrs; /* 1: row_ptr, col_idx, values, b are device pointers    */
+    int32_t reserved;    /* must be 0                                             */
+    void *stream;        /* cudaStream_t for the set-up work; NULL = default      */
+} asyrk_lsq_opts;
+
+/* Create the problem of the system above from A (m x n CSR, as for
+ * asyrk_create except that rows of A may be empty) and b (m doubles).  The
+ * system has one row per non-empty column of A (entries (n + i, phi A_ij), i
+ * ascending; right side phi sum_i A_ij b_i in FP64, ascending i, no fused
+ * multiply-adds), then one per row i of A (a_i, then (n + i, -zeta); right
+ * side 0); a column of zeros would give the row 0 = 0 and is left out.  Values
+ * are stored in vdtype (phi A_ij and -zeta rounded to nearest; BF16 through
+ * FP32).  Solve it with asyrk_solve on an iterate of n + m doubles, then read
+ * x_LS with asyrk_lsq_solution.  Host arrays are read before the call returns.
+ * Errors: EINVAL (m, n < 1, m + n > 2^31-1, more than 2^32-1 nonzeros, a
+ * malformed CSR, non-finite data, zeta <= 0, phi < 0, opts NULL), ENOMEM,
+ * ECUDA.  On error *out is NULL. */
+int asyrk_lsq_create(asyrk_problem **out, int64_t m, int64_t n, const int64_t *row_ptr,
+                     const int32_t *col_idx, const void *values, int vdtype, const double *b,
+                     const asyrk_lsq_opts *opts);
+
+/* x_LS = x-block of z / zeta for a problem made by asyrk_lsq_create; z has
+ * n + m doubles, x_ls n doubles, both on the host or both on the device
+ * (on_device).  Errors: EINVAL (NULL, not a least-squares problem), ENOMEM,
+ * ECUDA. */
+int asyrk_lsq_solution(asyrk_problem *p, const double *z, int on_device, double *x_ls);
+
 /* Largest m accepted by asyrk_residual_noalloc. */
 #define ASYRK_NOALLOC_MAX_ROWS 16777216
 

@@ -38,6 +38,12 @@ class CreateOpts(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
+class LsqOpts(ctypes.Structure):
+    _fields_ = [("zeta", ctypes.c_double), ("phi", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("device_ptrs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("device_ptrs", ctypes.c_int32),
                 ("workers", ctypes.c_int32), ("subwarp", ctypes.c_int32),
@@ -79,7 +85,7 @@ EXPORTS = ["asyrk_create", "asyrk_destroy", "asyrk_solve", "asyrk_residual", "as
            "asyrk_residual_noalloc", "asyrk_normal_residual", "asyrk_autotune", "asyrk_batch_create", "asyrk_batch_solve",
            "asyrk_batch_destroy", "asyrk_server_create", "asyrk_server_submit",
            "asyrk_server_wait", "asyrk_server_cancel", "asyrk_server_get_stats",
-           "asyrk_server_destroy"]
+           "asyrk_server_destroy", "asyrk_lsq_create", "asyrk_lsq_solution"]
 NOALLOC_MAX_ROWS = 16777216
 PROBE_RED_F32, PROBE_GATHER_F32, PROBE_GATHER_RED, PROBE_STREAM = 0, 1, 2, 3
 
@@ -99,6 +105,11 @@ def load(path: str = LIB_PATH):
     lib.asyrk_create.argtypes = [ctypes.POINTER(P), i64, i64, P, P, P, ctypes.c_int, P,
                                  ctypes.POINTER(CreateOpts)]
     lib.asyrk_create.restype = ctypes.c_int
+    lib.asyrk_lsq_create.argtypes = [ctypes.POINTER(P), i64, i64, P, P, P, ctypes.c_int, P,
+                                     ctypes.POINTER(LsqOpts)]
+    lib.asyrk_lsq_create.restype = ctypes.c_int
+    lib.asyrk_lsq_solution.argtypes = [P, P, ctypes.c_int, P]
+    lib.asyrk_lsq_solution.restype = ctypes.c_int
     lib.asyrk_destroy.argtypes = [P]
     lib.asyrk_destroy.restype = None
     lib.asyrk_solve.argtypes = [P, P, f64, f64, i64, ctypes.POINTER(SolveOpts),
@@ -245,6 +256,21 @@ def asyrk_create(m, n, row_ptr, col_idx, values, vdtype, b, seed=0, device_ptrs=
     st = load().asyrk_create(ctypes.byref(h), m, n, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
                              vdtype, _ptr(b), ctypes.byref(o))
     return st, h
+
+
+def asyrk_lsq_create(m, n, row_ptr, col_idx, values, vdtype, b, zeta, phi=1.0, seed=0,
+                     device_ptrs=False, stream=None):
+    """Section 6's least-squares system; returns (status, handle)."""
+    h = ctypes.c_void_p()
+    o = LsqOpts(zeta=float(zeta), phi=float(phi), seed=seed, device_ptrs=1 if device_ptrs else 0,
+                reserved=0, stream=_stream(stream))
+    st = load().asyrk_lsq_create(ctypes.byref(h), m, n, _ptr(row_ptr), _ptr(col_idx),
+                                 _ptr(values), vdtype, _ptr(b), ctypes.byref(o))
+    return st, h
+
+
+def asyrk_lsq_solution(h, z, x_out, on_device=False):
+    return load().asyrk_lsq_solution(h, _ptr(z), 1 if on_device else 0, _ptr(x_out))
 
 
 def asyrk_destroy(h):
@@ -428,6 +454,37 @@ class Problem:
             seed = synth.solver_seed(s.seed)
         return cls(s.m, s.n, s.row_ptr, s.col, s.val_store, DTYPES[s.value_dtype], s.b, seed=seed,
                    **kw)
+
+    @classmethod
+    def lsq(cls, m, n, row_ptr, col_idx, values, vdtype, b, zeta, phi=1.0, seed=0,
+            device_ptrs=False, stream=None):
+        """Section 6's square consistent system for min ||A x - b|| (A: m x n).
+
+        The problem's iterate has n + m entries; ``lsq_solution`` maps it to x_LS."""
+        if isinstance(vdtype, str):
+            vdtype = DTYPES[vdtype]
+        st, h = asyrk_lsq_create(m, n, row_ptr, col_idx, values, vdtype, b, zeta, phi=phi,
+                                 seed=seed, device_ptrs=device_ptrs, stream=stream)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_lsq_create")
+        self = cls.__new__(cls)
+        self.h = h
+        st, stats = asyrk_problem_get_stats(h)
+        self.m, self.n = stats.m, stats.n
+        self.lsq_n = n
+        return self
+
+    def lsq_solution(self, z, on_device=False):
+        """x_LS from the iterate z of a least-squares problem (numpy or torch like z)."""
+        if on_device:
+            import torch
+            x = torch.empty(self.lsq_n, dtype=torch.float64, device=z.device)
+        else:
+            x = np.empty(self.lsq_n, dtype=np.float64)
+        st = asyrk_lsq_solution(self.h, z, x, on_device)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_lsq_solution")
+        return x
 
     def close(self):
         if self.h is not None and self.h.value:

@@ -1,0 +1,523 @@
+// lsq.cu -- least squares through a square consistent system (Section 6).
+//
+// min ||A x - b|| is solved by the method applied to
+//     [ 0   phi A^T ] [x]   [phi A^T b]
+//     [ A   -zeta I ] [y] = [    0    ]
+// whose solutions have x = zeta x_LS and y = A x_LS.  Rows, in order: one per
+// non-empty column j of A (entries (n + i, phi A_ij), i ascending; right side
+// phi * sum_i A_ij b_i summed in ascending i in FP64 without fused
+// multiply-adds); then one per row i of A (its entries, then (n + i, -zeta);
+// right side 0).  A column of zeros would give the row 0 = 0 and is left out.
+//
+// The system is assembled on the GPU: a stable LSD radix sort of the entries
+// by column gives A^T in CSR with rows ascending inside each column, two
+// fills write the two blocks, and the result goes through asyrk_create.
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace asyrk {
+
+namespace {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 8;  // keys per thread; a warp owns 8 rounds of 32 consecutive keys
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SCAN_TILE = 2048;
+
+__device__ __forceinline__ double widen_v(double v) { return v; }
+__device__ __forceinline__ double widen_v(float v) { return (double)v; }
+__device__ __forceinline__ double widen_v(bf16_t v)
+{
+    return (double)__uint_as_float(((unsigned)v.bits) << 16);
+}
+__device__ __forceinline__ void narrow_v(double d, double &v) { v = d; }
+__device__ __forceinline__ void narrow_v(double d, float &v) { v = (float)d; }
+__device__ __forceinline__ void narrow_v(double d, bf16_t &v)
+{
+    // round to nearest even from FP32 (the FP64 value is first rounded to FP32)
+    const unsigned u = __float_as_uint((float)d);
+    v.bits = (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+
+enum : unsigned { BAD_COL = 1u, BAD_ORDER = 2u, BAD_VAL = 4u, BAD_B = 8u };
+
+// ---- device-wide exclusive scan of int64 (three passes) -------------------
+__global__ void k_scan_tiles(const int64_t *__restrict__ in, int64_t *__restrict__ out,
+                             int64_t *__restrict__ tile_sum, int64_t count)
+{
+    __shared__ int64_t part[SCAN_TILE / 8];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    const int t = threadIdx.x;  // 256 threads, 8 items each
+    int64_t v[8], run = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int64_t q = base + t * 8 + k;
+        v[k] = q < count ? in[q] : 0;
+        run += v[k];
+    }
+    part[t] = run;
+    __syncthreads();
+    if (t == 0) {
+        int64_t acc = 0;
+        for (int w = 0; w < SCAN_TILE / 8; ++w) {
+            const int64_t x = part[w];
+            part[w] = acc;
+            acc += x;
+        }
+        tile_sum[blockIdx.x] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[t];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int64_t q = base + t * 8 + k;
+        if (q < count) out[q] = acc;
+        acc += v[k];
+    }
+}
+
+__global__ void k_scan_sums(int64_t *__restrict__ tile_sum, int64_t tiles, int64_t *__restrict__ total)
+{
+    // one thread: tile counts are small (count / 2048)
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t acc = 0;
+    for (int64_t k = 0; k < tiles; ++k) {
+        const int64_t x = tile_sum[k];
+        tile_sum[k] = acc;
+        acc += x;
+    }
+    *total = acc;
+}
+
+__global__ void k_scan_add(int64_t *__restrict__ out, const int64_t *__restrict__ tile_sum,
+                           int64_t count)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < count) out[q] += tile_sum[q / SCAN_TILE];
+}
+
+// out[0..count) = exclusive scan of in; *total = the sum.  tmp holds
+// ceil(count / SCAN_TILE) entries.
+int exclusive_scan(const int64_t *in, int64_t *out, int64_t count, int64_t *tmp, int64_t *total,
+                   cudaStream_t s)
+{
+    const int64_t tiles = (count + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 0) {
+        ASYRK_CK(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
+        return ASYRK_OK;
+    }
+    k_scan_tiles<<<(unsigned)tiles, 256, 0, s>>>(in, out, tmp, count);
+    k_scan_sums<<<1, 32, 0, s>>>(tmp, tiles, total);
+    k_scan_add<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, tmp, count);
+    ASYRK_CK(cudaGetLastError());
+    return ASYRK_OK;
+}
+
+// ---- stable LSD radix sort of (key, value) by 8-bit digits ----------------
+// Tile t holds keys [t*SORT_TILE, (t+1)*SORT_TILE); inside it warp w holds
+// SORT_ITEMS rounds of 32 consecutive keys starting at w*32*SORT_ITEMS, so
+// (warp, round, lane) is the input order and the scatter keeps it.
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t *__restrict__ keys,
+                                                            int64_t count, int shift,
+                                                            int64_t *__restrict__ hist,
+                                                            int64_t tiles)
+{
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    for (int k = threadIdx.x; k < SORT_TILE; k += SORT_THREADS) {
+        const int64_t q = base + k;
+        if (q < count) atomicAdd(&h[(keys[q] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    // digit-major, so one exclusive scan gives every (digit, tile) its offset
+    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(
+    const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t count, int shift,
+    const int64_t *__restrict__ offs, int64_t tiles, uint32_t *__restrict__ keys_out,
+    uint32_t *__restrict__ vals_out)
+{
+    __shared__ unsigned wcnt[SORT_WARPS][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)w * 32 * SORT_ITEMS;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t k_[SORT_ITEMS], v_[SORT_ITEMS];
+    unsigned rank[SORT_ITEMS];
+    int dig[SORT_ITEMS];
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int64_t q = base + r * 32 + lane;
+        const bool in = q < count;
+        k_[r] = in ? keys[q] : 0u;
+        v_[r] = in ? vals[q] : 0u;
+        dig[r] = in ? (int)((k_[r] >> shift) & 255u) : 256;  // 256: no key
+        const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+        const unsigned before = (in ? wcnt[w][dig[r]] : 0u);
+        rank[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (in && (peers & lt) == 0) wcnt[w][dig[r]] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {  // per digit: exclusive scan over the warps
+        const int d = threadIdx.x;
+        unsigned run = 0;
+        for (int ww = 0; ww < SORT_WARPS; ++ww) {
+            const unsigned c = wcnt[ww][d];
+            wcnt[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        if (dig[r] == 256) continue;
+        const int64_t pos = offs[(int64_t)dig[r] * tiles + blockIdx.x] + wcnt[w][dig[r]] + rank[r];
+        keys_out[pos] = k_[r];
+        vals_out[pos] = v_[r];
+    }
+}
+
+// ---- the system's pieces ------------------------------------------------
+// One thread per row of A: checks, the entry -> row map, column counts.
+template <typename VT>
+__global__ void k_lsq_rows(int64_t m, int64_t n, const int64_t *__restrict__ rp,
+                           const int32_t *__restrict__ col, const VT *__restrict__ val,
+                           const double *__restrict__ b, uint32_t *__restrict__ row_of,
+                           int64_t *__restrict__ ccount, unsigned *__restrict__ err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    unsigned bad = 0;
+    int32_t prev = -1;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const int32_t c = col[k];
+        if (c < 0 || (int64_t)c >= n) {
+            bad |= BAD_COL;
+            continue;
+        }
+        if (c <= prev) bad |= BAD_ORDER;
+        prev = c;
+        if (!isfinite(widen_v(val[k]))) bad |= BAD_VAL;
+        row_of[k] = (uint32_t)i;
+        atomicAdd((unsigned long long *)&ccount[c], 1ull);
+    }
+    if (!isfinite(b[i])) bad |= BAD_B;
+    if (bad) atomicOr(err, bad);
+}
+
+__global__ void k_iota_u32(uint32_t *__restrict__ v, int64_t count)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < count) v[q] = (uint32_t)q;
+}
+
+__global__ void k_nonempty(const int64_t *__restrict__ ccount, int64_t n, int64_t *__restrict__ flag)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) flag[j] = ccount[j] > 0 ? 1 : 0;
+}
+
+// A^T block: sorted position p holds entry k = perm[p] of column j = key[p].
+template <typename VT>
+__global__ void k_lsq_first_block(int64_t nnz, int64_t n, const uint32_t *__restrict__ perm,
+                                  const uint32_t *__restrict__ row_of, const VT *__restrict__ val,
+                                  double phi, int32_t *__restrict__ acol, VT *__restrict__ aval)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnz) return;
+    const uint32_t k = perm[p];
+    acol[p] = (int32_t)(n + row_of[k]);
+    VT v;
+    if (phi == 1.0) {
+        v = val[k];
+    } else {
+        narrow_v(__dmul_rn(phi, widen_v(val[k])), v);
+    }
+    aval[p] = v;
+}
+
+// One thread per column: its row's start and phi * (A^T b)_j in ascending i.
+template <typename VT>
+__global__ void k_lsq_rhs(int64_t n, const int64_t *__restrict__ ccount,
+                          const int64_t *__restrict__ cstart, const int64_t *__restrict__ rowidx,
+                          const uint32_t *__restrict__ perm, const uint32_t *__restrict__ row_of,
+                          const VT *__restrict__ val, const double *__restrict__ b, double phi,
+                          int64_t *__restrict__ arp, double *__restrict__ ab)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || ccount[j] == 0) return;
+    double s = 0.0;
+    for (int64_t p = cstart[j]; p < cstart[j] + ccount[j]; ++p) {
+        const uint32_t k = perm[p];
+        s = __dadd_rn(s, __dmul_rn(widen_v(val[k]), b[row_of[k]]));
+    }
+    const int64_t r = rowidx[j];
+    arp[r] = cstart[j];
+    ab[r] = __dmul_rn(phi, s);
+}
+
+// One thread per row i of A: row nne + i of the system, [a_i, -zeta e_i].
+template <typename VT>
+__global__ void k_lsq_second_block(int64_t m, int64_t n, int64_t nne, int64_t nnz,
+                                   const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                   const VT *__restrict__ val, double zeta,
+                                   int64_t *__restrict__ arp, int32_t *__restrict__ acol,
+                                   VT *__restrict__ aval, double *__restrict__ ab)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int64_t d = nnz + rp[i] + i;
+    arp[nne + i] = d;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k, ++d) {
+        acol[d] = col[k];
+        aval[d] = val[k];
+    }
+    acol[d] = (int32_t)(n + i);
+    VT z;
+    narrow_v(-zeta, z);
+    aval[d] = z;
+    ab[nne + i] = 0.0;
+    if (i == m - 1) arp[nne + m] = d + 1;
+}
+
+__global__ void k_lsq_extract(const double *__restrict__ z, int64_t n, double zeta,
+                              double *__restrict__ x)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) x[j] = __ddiv_rn(z[j], zeta);
+}
+
+inline unsigned grid_for(int64_t count, int threads = 256)
+{
+    return (unsigned)((count + threads - 1) / threads);
+}
+
+// device buffers freed on every exit path
+struct DevTmp {
+    std::vector<void *> ptrs;
+    template <typename T>
+    int alloc(T **p, size_t count)
+    {
+        *p = nullptr;
+        cudaError_t e = cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            (void)cudaGetLastError();
+            return set_error(e == cudaErrorMemoryAllocation ? ASYRK_ENOMEM : ASYRK_ECUDA,
+                             "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                             cudaGetErrorString(e));
+        }
+        ptrs.push_back((void *)*p);
+        return ASYRK_OK;
+    }
+    ~DevTmp()
+    {
+        for (void *q : ptrs) cudaFree(q);
+    }
+};
+
+size_t dtype_size(int dtype)
+{
+    return dtype == ASYRK_F64 ? 8 : dtype == ASYRK_F32 ? 4 : 2;
+}
+
+}  // namespace
+
+template <typename VT>
+static int lsq_build(asyrk_problem **out, int64_t m, int64_t n, int64_t nnz,
+                     const int64_t *rp_d, const int32_t *col_d, const VT *val_d,
+                     const double *b_d, int vdtype, const asyrk_lsq_opts &o, cudaStream_t s)
+{
+    const double phi = o.phi == 0.0 ? 1.0 : o.phi;
+    DevTmp t;
+    int st;
+    uint32_t *row_of, *keys[2], *perm[2];
+    int64_t *ccount, *cstart, *flag, *rowidx, *hist, *offs, *scan_tmp, *totals;
+    unsigned *err;
+    const int64_t tiles = (nnz + SORT_TILE - 1) / SORT_TILE;
+    const int64_t scan_max = (256 * tiles > n ? 256 * tiles : n);
+    if ((st = t.alloc(&row_of, (size_t)nnz)) || (st = t.alloc(&keys[0], (size_t)nnz)) ||
+        (st = t.alloc(&keys[1], (size_t)nnz)) || (st = t.alloc(&perm[0], (size_t)nnz)) ||
+        (st = t.alloc(&perm[1], (size_t)nnz)) || (st = t.alloc(&ccount, (size_t)n)) ||
+        (st = t.alloc(&cstart, (size_t)n)) || (st = t.alloc(&flag, (size_t)n)) ||
+        (st = t.alloc(&rowidx, (size_t)n)) || (st = t.alloc(&hist, (size_t)(256 * tiles))) ||
+        (st = t.alloc(&offs, (size_t)(256 * tiles))) ||
+        (st = t.alloc(&scan_tmp, (size_t)(scan_max / SCAN_TILE + 1))) ||
+        (st = t.alloc(&totals, 2)) || (st = t.alloc(&err, 1)))
+        return st;
+
+    // 1. checks, entry -> row map, column counts
+    ASYRK_CK(cudaMemsetAsync(ccount, 0, n * sizeof(int64_t), s));
+    ASYRK_CK(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+    k_lsq_rows<VT><<<grid_for(m), 256, 0, s>>>(m, n, rp_d, col_d, val_d, b_d, row_of, ccount, err);
+    ASYRK_CK(cudaGetLastError());
+    unsigned bad = 0;
+    ASYRK_CK(cudaMemcpyAsync(&bad, err, sizeof bad, cudaMemcpyDeviceToHost, s));
+    ASYRK_CK(cudaStreamSynchronize(s));
+    if (bad & BAD_COL) return set_error(ASYRK_EINVAL, "a column index is outside [0, n)");
+    if (bad & BAD_ORDER) return set_error(ASYRK_EINVAL, "column indices not strictly ascending in a row");
+    if (bad & BAD_VAL) return set_error(ASYRK_EINVAL, "a value is not finite");
+    if (bad & BAD_B) return set_error(ASYRK_EINVAL, "b is not finite");
+
+    // 2. entries sorted by column, stable, so rows ascend inside each column
+    int cur = 0;
+    if (nnz > 0) {
+        ASYRK_CK(cudaMemcpyAsync(keys[0], col_d, nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+        k_iota_u32<<<grid_for(nnz), 256, 0, s>>>(perm[0], nnz);
+        ASYRK_CK(cudaGetLastError());
+        int bits = 0;
+        while (bits < 32 && ((uint64_t)(n - 1) >> bits) != 0) ++bits;
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_radix_hist<<<(unsigned)tiles, SORT_THREADS, 0, s>>>(keys[cur], nnz, shift, hist, tiles);
+            ASYRK_CK(cudaGetLastError());
+            if ((st = exclusive_scan(hist, offs, 256 * tiles, scan_tmp, totals, s)) != ASYRK_OK)
+                return st;
+            k_radix_scatter<<<(unsigned)tiles, SORT_THREADS, 0, s>>>(
+                keys[cur], perm[cur], nnz, shift, offs, tiles, keys[cur ^ 1], perm[cur ^ 1]);
+            ASYRK_CK(cudaGetLastError());
+            cur ^= 1;
+        }
+    }
+
+    // 3. column starts and the row number of each non-empty column
+    if ((st = exclusive_scan(ccount, cstart, n, scan_tmp, totals, s)) != ASYRK_OK) return st;
+    k_nonempty<<<grid_for(n), 256, 0, s>>>(ccount, n, flag);
+    ASYRK_CK(cudaGetLastError());
+    if ((st = exclusive_scan(flag, rowidx, n, scan_tmp, totals + 1, s)) != ASYRK_OK) return st;
+    int64_t nne = 0;
+    ASYRK_CK(cudaMemcpyAsync(&nne, totals + 1, sizeof nne, cudaMemcpyDeviceToHost, s));
+    ASYRK_CK(cudaStreamSynchronize(s));
+
+    // 4. the system
+    const int64_t rows = nne + m, annz = 2 * nnz + m;
+    int64_t *arp;
+    int32_t *acol;
+    VT *aval;
+    double *ab;
+    if ((st = t.alloc(&arp, (size_t)rows + 1)) || (st = t.alloc(&acol, (size_t)annz)) ||
+        (st = t.alloc(&aval, (size_t)annz)) || (st = t.alloc(&ab, (size_t)rows)))
+        return st;
+    if (nnz > 0) {
+        k_lsq_first_block<VT><<<grid_for(nnz), 256, 0, s>>>(nnz, n, perm[cur], row_of, val_d, phi,
+                                                            acol, aval);
+        k_lsq_rhs<VT><<<grid_for(n), 256, 0, s>>>(n, ccount, cstart, rowidx, perm[cur], row_of,
+                                                  val_d, b_d, phi, arp, ab);
+    }
+    k_lsq_second_block<VT><<<grid_for(m), 256, 0, s>>>(m, n, nne, nnz, rp_d, col_d, val_d, o.zeta,
+                                                       arp, acol, aval, ab);
+    ASYRK_CK(cudaGetLastError());
+    ASYRK_CK(cudaStreamSynchronize(s));
+
+    asyrk_create_opts co;
+    memset(&co, 0, sizeof co);
+    co.seed = o.seed;
+    co.device_ptrs = 1;
+    co.stream = o.stream;
+    asyrk_problem *p = nullptr;
+    if ((st = asyrk_create(&p, rows, n + m, arp, acol, aval, vdtype, ab, &co)) != ASYRK_OK) return st;
+    p->lsq_n = n;
+    p->lsq_zeta = o.zeta;
+    *out = p;
+    return ASYRK_OK;
+}
+
+}  // namespace asyrk
+
+using namespace asyrk;
+
+extern "C" int asyrk_lsq_create(asyrk_problem **out, int64_t m, int64_t n, const int64_t *row_ptr,
+                                const int32_t *col_idx, const void *values, int vdtype,
+                                const double *b, const asyrk_lsq_opts *opts)
+{
+    if (!out) return set_error(ASYRK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!opts) return set_error(ASYRK_EINVAL, "opts is NULL (zeta has no default)");
+    const asyrk_lsq_opts o = *opts;
+    if (m <= 0 || n <= 0 || m + n > 0x7fffffffLL)
+        return set_error(ASYRK_EINVAL, "m, n >= 1 and m + n <= 2^31-1 required");
+    if (!row_ptr || !col_idx || !values || !b) return set_error(ASYRK_EINVAL, "NULL array");
+    if (vdtype != ASYRK_F64 && vdtype != ASYRK_F32 && vdtype != ASYRK_BF16)
+        return set_error(ASYRK_EINVAL, "unknown value dtype %d", vdtype);
+    if (!(o.zeta > 0.0) || !isfinite(o.zeta)) return set_error(ASYRK_EINVAL, "zeta must be > 0");
+    if (o.phi < 0.0 || !isfinite(o.phi)) return set_error(ASYRK_EINVAL, "phi must be > 0 (0: 1)");
+    if (o.reserved != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
+    cudaStream_t s = (cudaStream_t)o.stream;
+
+    std::vector<int64_t> rp((size_t)m + 1);
+    if (o.device_ptrs)
+        ASYRK_CK(cudaMemcpy(rp.data(), row_ptr, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    else
+        memcpy(rp.data(), row_ptr, (m + 1) * sizeof(int64_t));
+    if (rp[0] != 0) return set_error(ASYRK_EINVAL, "row_ptr[0] must be 0");
+    for (int64_t i = 0; i < m; ++i)
+        if (rp[i + 1] < rp[i] || rp[i + 1] - rp[i] > n)
+            return set_error(ASYRK_EINVAL, "row_ptr decreases or row %lld is longer than n",
+                             (long long)i);
+    const int64_t nnz = rp[m];
+    if (nnz > 0xffffffffLL) return set_error(ASYRK_EINVAL, "more than 2^32-1 nonzeros");
+
+    DevTmp t;
+    const size_t es = dtype_size(vdtype);
+    const int64_t *rp_d = row_ptr;
+    const int32_t *col_d = col_idx;
+    const void *val_d = values;
+    const double *b_d = b;
+    if (!o.device_ptrs) {
+        int64_t *a;
+        int32_t *c;
+        char *v;
+        double *bb;
+        int st;
+        if ((st = t.alloc(&a, (size_t)m + 1)) || (st = t.alloc(&c, (size_t)nnz)) ||
+            (st = t.alloc(&v, (size_t)nnz * es)) || (st = t.alloc(&bb, (size_t)m)))
+            return st;
+        ASYRK_CK(cudaMemcpyAsync(a, rp.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        ASYRK_CK(cudaMemcpyAsync(c, col_idx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        ASYRK_CK(cudaMemcpyAsync(v, values, nnz * es, cudaMemcpyHostToDevice, s));
+        ASYRK_CK(cudaMemcpyAsync(bb, b, m * sizeof(double), cudaMemcpyHostToDevice, s));
+        rp_d = a;
+        col_d = c;
+        val_d = v;
+        b_d = bb;
+    }
+    switch (vdtype) {
+    case ASYRK_F64:
+        return lsq_build<double>(out, m, n, nnz, rp_d, col_d, (const double *)val_d, b_d, vdtype, o, s);
+    case ASYRK_F32:
+        return lsq_build<float>(out, m, n, nnz, rp_d, col_d, (const float *)val_d, b_d, vdtype, o, s);
+    default:
+        return lsq_build<bf16_t>(out, m, n, nnz, rp_d, col_d, (const bf16_t *)val_d, b_d, vdtype, o, s);
+    }
+}
+
+extern "C" int asyrk_lsq_solution(asyrk_problem *p, const double *z, int on_device, double *x_ls)
+{
+    if (!p || !z || !x_ls) return set_error(ASYRK_EINVAL, "NULL argument");
+    if (p->lsq_n <= 0) return set_error(ASYRK_EINVAL, "not a least-squares problem");
+    const int64_t n = p->lsq_n;
+    if (on_device) {
+        k_lsq_extract<<<grid_for(n), 256>>>(z, n, p->lsq_zeta, x_ls);
+        ASYRK_CK(cudaGetLastError());
+        ASYRK_CK(cudaDeviceSynchronize());
+        return ASYRK_OK;
+    }
+    DevTmp t;
+    double *zd, *xd;
+    int st;
+    if ((st = t.alloc(&zd, (size_t)n)) || (st = t.alloc(&xd, (size_t)n))) return st;
+    ASYRK_CK(cudaMemcpy(zd, z, n * sizeof(double), cudaMemcpyHostToDevice));
+    k_lsq_extract<<<grid_for(n), 256>>>(zd, n, p->lsq_zeta, xd);
+    ASYRK_CK(cudaGetLastError());
+    ASYRK_CK(cudaMemcpy(x_ls, xd, n * sizeof(double), cudaMemcpyDeviceToHost));
+    return ASYRK_OK;
+}

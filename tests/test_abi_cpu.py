@@ -50,6 +50,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(asyrk.SolveInfo) == 96
     assert ctypes.sizeof(asyrk.ProblemStats) == 80
     assert ctypes.sizeof(asyrk.BatchOpts) == 24
+    assert ctypes.sizeof(asyrk.LsqOpts) == 40
     assert ctypes.sizeof(asyrk.BatchInfo) == 56
     assert ctypes.sizeof(asyrk.TuneResult) == 24
     assert ctypes.sizeof(asyrk.ServerOpts) == 32
