@@ -404,7 +404,9 @@ typedef struct asyrk_lsq_opts {
  * multiply-adds), then one per row i of A (a_i, then (n + i, -zeta); right
  * side 0); a column of zeros would give the row 0 = 0 and is left out.  Values
  * are stored in vdtype (phi A_ij and -zeta rounded to nearest; BF16 through
- * FP32).  Solve it with asyrk_solve on an iterate of n + m doubles, then read
+ * FP32); with FP32/BF16 values the A^T block is phi A exactly only when phi is
+ * a power of two (phi = 1 is Section 6's choice), otherwise it carries the
+ * rounding of phi A_ij.  Solve it with asyrk_solve on an iterate of n + m doubles, then read
  * x_LS with asyrk_lsq_solution.  Host arrays are read before the call returns.
  * Errors: EINVAL (m, n < 1, m + n > 2^31-1, more than 2^32-1 nonzeros, a
  * malformed CSR, non-finite data, zeta <= 0, phi < 0, opts NULL), ENOMEM,
@@ -413,7 +415,9 @@ int asyrk_lsq_create(asyrk_problem **out, int64_t m, int64_t n, const int64_t *r
                      const int32_t *col_idx, const void *values, int vdtype, const double *b,
                      const asyrk_lsq_opts *opts);
 
-/* x_LS = x-block of z / zeta for a problem made by asyrk_lsq_create; z has
+/* x_LS = x-block of z / zeta_s for a problem made by asyrk_lsq_create, zeta_s
+ * being zeta as the system stores it (rounded to vdtype, so that the identity
+ * x = zeta_s x_LS is exact for the stored system); z has
  * n + m doubles, x_ls n doubles, both on the host or both on the device
  * (on_device).  Errors: EINVAL (NULL, not a least-squares problem), ENOMEM,
  * ECUDA. */

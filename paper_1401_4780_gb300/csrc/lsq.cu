@@ -331,6 +331,21 @@ size_t dtype_size(int dtype)
     return dtype == ASYRK_F64 ? 8 : dtype == ASYRK_F32 ? 4 : 2;
 }
 
+// v as the system stores it (the host twin of narrow_v): x = zeta_s x_LS holds
+// for the stored zeta_s, so the solution is read back with that value.
+double stored_value(int dtype, double v)
+{
+    if (dtype == ASYRK_F64) return v;
+    const float f = (float)v;
+    if (dtype == ASYRK_F32) return (double)f;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = ((u + 0x7fffu + ((u >> 16) & 1u)) >> 16) << 16;
+    float g;
+    memcpy(&g, &u, 4);
+    return (double)g;
+}
+
 }  // namespace
 
 template <typename VT>
@@ -426,7 +441,7 @@ static int lsq_build(asyrk_problem **out, int64_t m, int64_t n, int64_t nnz,
     asyrk_problem *p = nullptr;
     if ((st = asyrk_create(&p, rows, n + m, arp, acol, aval, vdtype, ab, &co)) != ASYRK_OK) return st;
     p->lsq_n = n;
-    p->lsq_zeta = o.zeta;
+    p->lsq_zeta = stored_value(vdtype, o.zeta);
     *out = p;
     return ASYRK_OK;
 }
