@@ -389,12 +389,14 @@ void asyrk_server_destroy(asyrk_server *s);
  * maximises lambda_min/||.||_F^2 of the system, the quantity the rate of
  * Theorem 2 depends on. */
 typedef struct asyrk_lsq_opts {
-    double zeta;         /* > 0, finite: the y-block scale                        */
-    double phi;          /* > 0: the A^T-block scale; 0 means 1                   */
-    uint64_t seed;       /* Philox key of the system's row sequence               */
-    int32_t device_ptrs; /* 1: row_ptr, col_idx, values, b are device pointers    */
-    int32_t reserved;    /* must be 0                                             */
-    void *stream;        /* cudaStream_t for the set-up work; NULL = default      */
+    double zeta;           /* > 0: the y-block scale; 0: Section 6's sigma_r/sqrt(2)
+                              with sigma_r from asyrk_spectrum_estimate            */
+    double phi;            /* > 0: the A^T-block scale; 0 means 1                   */
+    uint64_t seed;         /* Philox key of the system's row sequence (and of the
+                              estimate's start vector)                              */
+    int32_t device_ptrs;   /* 1: row_ptr, col_idx, values, b are device pointers    */
+    int32_t lanczos_steps; /* steps of the sigma_r estimate when zeta = 0; 0: 100   */
+    void *stream;          /* cudaStream_t for the set-up work; NULL = default      */
 } asyrk_lsq_opts;
 
 /* Create the problem of the system above from A (m x n CSR, as for
@@ -409,8 +411,9 @@ typedef struct asyrk_lsq_opts {
  * rounding of phi A_ij.  Solve it with asyrk_solve on an iterate of n + m doubles, then read
  * x_LS with asyrk_lsq_solution.  Host arrays are read before the call returns.
  * Errors: EINVAL (m, n < 1, m + n > 2^31-1, more than 2^32-1 nonzeros, a
- * malformed CSR, non-finite data, zeta <= 0, phi < 0, opts NULL), ENOMEM,
- * ECUDA.  On error *out is NULL. */
+ * malformed CSR, non-finite data, zeta < 0, phi < 0, lanczos_steps < 0, opts
+ * NULL, A without a nonzero when zeta = 0), ENOMEM, ECUDA.  On error *out is
+ * NULL. */
 int asyrk_lsq_create(asyrk_problem **out, int64_t m, int64_t n, const int64_t *row_ptr,
                      const int32_t *col_idx, const void *values, int vdtype, const double *b,
                      const asyrk_lsq_opts *opts);
@@ -422,6 +425,29 @@ int asyrk_lsq_create(asyrk_problem **out, int64_t m, int64_t n, const int64_t *r
  * (on_device).  Errors: EINVAL (NULL, not a least-squares problem), ENOMEM,
  * ECUDA. */
 int asyrk_lsq_solution(asyrk_problem *p, const double *z, int on_device, double *x_ls);
+
+/* zeta (as stored) and phi of a least-squares problem; either pointer may be
+ * NULL.  Errors: EINVAL (NULL problem, not a least-squares problem). */
+int asyrk_lsq_params(const asyrk_problem *p, double *zeta, double *phi);
+
+/* Estimates of the smallest NONZERO eigenvalue and the largest eigenvalue of
+ * A^T A (Section 1's lambda_min and lambda_max; sigma_r^2 of Section 6), from
+ * `steps` Lanczos steps (0: 100) with full reorthogonalisation on the GPU,
+ * started from A^T u with u a random sign vector (Philox, key seed), so the
+ * Krylov space lies in the row space of A and null-space directions are left
+ * out (Ritz values under 1e-10 lambda_max are passed over as rounding-level
+ * null-space components).  Ritz values lie inside the spectrum: the estimates
+ * satisfy lambda_min <= *lambda_min and *lambda_max <= lambda_max up to
+ * rounding, and converge to them as steps grows (fast at both ends for the
+ * random sparse matrices of Section 5 when m/n is away from 1).  A is an
+ * m x n CSR as for asyrk_lsq_create (empty rows allowed), on the host or the
+ * device (device_ptrs); work runs on `stream` (a cudaStream_t, NULL = default);
+ * the device needs n (steps + 1) doubles for the Lanczos basis.
+ * Errors: EINVAL (dimensions, malformed CSR, non-finite values, steps < 0,
+ * A without a nonzero), ENOMEM, ECUDA. */
+int asyrk_spectrum_estimate(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                            const void *values, int vdtype, int device_ptrs, int32_t steps,
+                            uint64_t seed, void *stream, double *lambda_min, double *lambda_max);
 
 /* Largest m accepted by asyrk_residual_noalloc. */
 #define ASYRK_NOALLOC_MAX_ROWS 16777216

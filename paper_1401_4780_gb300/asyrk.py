@@ -40,7 +40,7 @@ class CreateOpts(ctypes.Structure):
 
 class LsqOpts(ctypes.Structure):
     _fields_ = [("zeta", ctypes.c_double), ("phi", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("device_ptrs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("device_ptrs", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -85,7 +85,8 @@ EXPORTS = ["asyrk_create", "asyrk_destroy", "asyrk_solve", "asyrk_residual", "as
            "asyrk_residual_noalloc", "asyrk_normal_residual", "asyrk_autotune", "asyrk_batch_create", "asyrk_batch_solve",
            "asyrk_batch_destroy", "asyrk_server_create", "asyrk_server_submit",
            "asyrk_server_wait", "asyrk_server_cancel", "asyrk_server_get_stats",
-           "asyrk_server_destroy", "asyrk_lsq_create", "asyrk_lsq_solution"]
+           "asyrk_server_destroy", "asyrk_lsq_create", "asyrk_lsq_solution",
+           "asyrk_lsq_params", "asyrk_spectrum_estimate"]
 NOALLOC_MAX_ROWS = 16777216
 PROBE_RED_F32, PROBE_GATHER_F32, PROBE_GATHER_RED, PROBE_STREAM = 0, 1, 2, 3
 
@@ -110,6 +111,12 @@ def load(path: str = LIB_PATH):
     lib.asyrk_lsq_create.restype = ctypes.c_int
     lib.asyrk_lsq_solution.argtypes = [P, P, ctypes.c_int, P]
     lib.asyrk_lsq_solution.restype = ctypes.c_int
+    lib.asyrk_lsq_params.argtypes = [P, ctypes.POINTER(f64), ctypes.POINTER(f64)]
+    lib.asyrk_lsq_params.restype = ctypes.c_int
+    lib.asyrk_spectrum_estimate.argtypes = [i64, i64, P, P, P, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int32, ctypes.c_uint64, P,
+                                            ctypes.POINTER(f64), ctypes.POINTER(f64)]
+    lib.asyrk_spectrum_estimate.restype = ctypes.c_int
     lib.asyrk_destroy.argtypes = [P]
     lib.asyrk_destroy.restype = None
     lib.asyrk_solve.argtypes = [P, P, f64, f64, i64, ctypes.POINTER(SolveOpts),
@@ -259,11 +266,11 @@ def asyrk_create(m, n, row_ptr, col_idx, values, vdtype, b, seed=0, device_ptrs=
 
 
 def asyrk_lsq_create(m, n, row_ptr, col_idx, values, vdtype, b, zeta, phi=1.0, seed=0,
-                     device_ptrs=False, stream=None):
-    """Section 6's least-squares system; returns (status, handle)."""
+                     device_ptrs=False, stream=None, lanczos_steps=0):
+    """Section 6's least-squares system (zeta = 0: estimated); returns (status, handle)."""
     h = ctypes.c_void_p()
     o = LsqOpts(zeta=float(zeta), phi=float(phi), seed=seed, device_ptrs=1 if device_ptrs else 0,
-                reserved=0, stream=_stream(stream))
+                lanczos_steps=lanczos_steps, stream=_stream(stream))
     st = load().asyrk_lsq_create(ctypes.byref(h), m, n, _ptr(row_ptr), _ptr(col_idx),
                                  _ptr(values), vdtype, _ptr(b), ctypes.byref(o))
     return st, h
@@ -271,6 +278,22 @@ def asyrk_lsq_create(m, n, row_ptr, col_idx, values, vdtype, b, zeta, phi=1.0, s
 
 def asyrk_lsq_solution(h, z, x_out, on_device=False):
     return load().asyrk_lsq_solution(h, _ptr(z), 1 if on_device else 0, _ptr(x_out))
+
+
+def asyrk_lsq_params(h):
+    z, f = ctypes.c_double(), ctypes.c_double()
+    st = load().asyrk_lsq_params(h, ctypes.byref(z), ctypes.byref(f))
+    return st, z.value, f.value
+
+
+def asyrk_spectrum_estimate(m, n, row_ptr, col_idx, values, vdtype, steps=0, seed=0,
+                            device_ptrs=False, stream=None):
+    """(status, lambda_min nonzero, lambda_max) of A^T A by Lanczos on the GPU."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    st = load().asyrk_spectrum_estimate(m, n, _ptr(row_ptr), _ptr(col_idx), _ptr(values), vdtype,
+                                        1 if device_ptrs else 0, steps, seed, _stream(stream),
+                                        ctypes.byref(lo), ctypes.byref(hi))
+    return st, lo.value, hi.value
 
 
 def asyrk_destroy(h):
@@ -456,15 +479,17 @@ class Problem:
                    **kw)
 
     @classmethod
-    def lsq(cls, m, n, row_ptr, col_idx, values, vdtype, b, zeta, phi=1.0, seed=0,
-            device_ptrs=False, stream=None):
+    def lsq(cls, m, n, row_ptr, col_idx, values, vdtype, b, zeta=0.0, phi=1.0, seed=0,
+            device_ptrs=False, stream=None, lanczos_steps=0):
         """Section 6's square consistent system for min ||A x - b|| (A: m x n).
 
+        zeta = 0 takes Section 6's sigma_r/sqrt(2) with sigma_r estimated on the GPU.
         The problem's iterate has n + m entries; ``lsq_solution`` maps it to x_LS."""
         if isinstance(vdtype, str):
             vdtype = DTYPES[vdtype]
         st, h = asyrk_lsq_create(m, n, row_ptr, col_idx, values, vdtype, b, zeta, phi=phi,
-                                 seed=seed, device_ptrs=device_ptrs, stream=stream)
+                                 seed=seed, device_ptrs=device_ptrs, stream=stream,
+                                 lanczos_steps=lanczos_steps)
         if st != OK:
             raise AsyrkError(st, "asyrk_lsq_create")
         self = cls.__new__(cls)
@@ -473,6 +498,13 @@ class Problem:
         self.m, self.n = stats.m, stats.n
         self.lsq_n = n
         return self
+
+    def lsq_params(self):
+        """(zeta as stored, phi) of a least-squares problem."""
+        st, z, f = asyrk_lsq_params(self.h)
+        if st != OK:
+            raise AsyrkError(st, "asyrk_lsq_params")
+        return z, f
 
     def lsq_solution(self, z, on_device=False):
         """x_LS from the iterate z of a least-squares problem (numpy or torch like z)."""

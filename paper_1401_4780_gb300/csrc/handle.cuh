@@ -22,7 +22,8 @@ struct asyrk_problem {
     bool rec_b_is_residual = false;  // rec[i].b currently holds a refinement residual
     int64_t launches = 0;            // kernels launched on behalf of this handle
     int64_t lsq_n = 0;               // > 0: the least-squares system of an m x lsq_n matrix
-    double lsq_zeta = 0.0;           //      and its y-block scale zeta
+    double lsq_zeta = 0.0;           //      its y-block scale zeta (as stored)
+    double lsq_phi = 0.0;            //      and its A^T-block scale phi
 
     RowRec *rec = nullptr;
     int32_t *col = nullptr;

@@ -12,6 +12,7 @@
 // The system is assembled on the GPU: a stable LSD radix sort of the entries
 // by column gives A^T in CSR with rows ascending inside each column, two
 // fills write the two blocks, and the result goes through asyrk_create.
+#include <math.h>
 #include <string.h>
 
 #include <vector>
@@ -211,7 +212,7 @@ __global__ void k_lsq_rows(int64_t m, int64_t n, const int64_t *__restrict__ rp,
         row_of[k] = (uint32_t)i;
         atomicAdd((unsigned long long *)&ccount[c], 1ull);
     }
-    if (!isfinite(b[i])) bad |= BAD_B;
+    if (b && !isfinite(b[i])) bad |= BAD_B;
     if (bad) atomicOr(err, bad);
 }
 
@@ -348,11 +349,261 @@ double stored_value(int dtype, double v)
 
 }  // namespace
 
-template <typename VT>
-static int lsq_build(asyrk_problem **out, int64_t m, int64_t n, int64_t nnz,
-                     const int64_t *rp_d, const int32_t *col_d, const VT *val_d,
-                     const double *b_d, int vdtype, const asyrk_lsq_opts &o, cudaStream_t s)
+// ---- Lanczos on A^T A (the estimate of sigma_r for zeta) -----------------
+__global__ void k_rand_sign(double *__restrict__ u, int64_t m, uint2 key)
 {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint4 r = philox4x32_10(make_uint4((unsigned)i, (unsigned)(i >> 32), 0x4c414eu, 2u), key);
+    u[i] = (r.x & 1u) ? 1.0 : -1.0;
+}
+
+template <typename VT>
+__global__ void k_spmv(int64_t m, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                       const VT *__restrict__ val, const double *__restrict__ v,
+                       double *__restrict__ y)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double s = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += widen_v(val[k]) * v[col[k]];
+    y[i] = s;
+}
+
+// w += A^T y (w zeroed by the caller); FP64 atomics, so the rounding order varies
+template <typename VT>
+__global__ void k_spmv_t(int64_t m, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                         const VT *__restrict__ val, const double *__restrict__ y,
+                         double *__restrict__ w)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double yi = y[i];
+    if (yi == 0.0) return;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) atomicAdd(&w[col[k]], widen_v(val[k]) * yi);
+}
+
+// out[j] = Q[:, j] . w for j < ncols (one block per column, fixed reduction order)
+__global__ void k_dot_cols(const double *__restrict__ Q, int64_t ld, const double *__restrict__ w,
+                           int64_t n, double *__restrict__ out)
+{
+    __shared__ double part[256];
+    const double *q = Q + (int64_t)blockIdx.x * ld;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) s += q[i] * w[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = part[0];
+}
+
+// w -= Q[:, 0:ncols] h
+__global__ void k_sub_cols(double *__restrict__ w, const double *__restrict__ Q, int64_t ld,
+                           int ncols, const double *__restrict__ h, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = w[i];
+    for (int j = 0; j < ncols; ++j) s -= Q[(int64_t)j * ld + i] * h[j];
+    w[i] = s;
+}
+
+__global__ void k_axpy_d(double *__restrict__ y, const double *__restrict__ x, double a, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += a * x[i];
+}
+
+__global__ void k_scale_d(double *__restrict__ y, const double *__restrict__ x, double a, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = a * x[i];
+}
+
+// number of eigenvalues below x of the symmetric tridiagonal (a, b), b[0] unused
+static int sturm_count(const std::vector<double> &a, const std::vector<double> &b, double x)
+{
+    int c = 0;
+    double d = 1.0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        d = a[i] - x - (i ? b[i] * b[i] / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++c;
+    }
+    return c;
+}
+
+// the k-th smallest eigenvalue (k from 1) by bisection on the Sturm count
+static double tridiag_eig(const std::vector<double> &a, const std::vector<double> &b, int k)
+{
+    double lo = a[0], hi = a[0];
+    for (size_t i = 0; i < a.size(); ++i) {  // Gershgorin
+        const double r = (i ? fabs(b[i]) : 0.0) + (i + 1 < a.size() ? fabs(b[i + 1]) : 0.0);
+        lo = fmin(lo, a[i] - r);
+        hi = fmax(hi, a[i] + r);
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * fmax(fabs(lo), fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(a, b, mid) >= k) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Extreme Ritz values of A^T A after `steps` Lanczos steps with full
+// reorthogonalisation (twice per step), started from A^T u so that the Krylov
+// space stays in the row space of A: lmin estimates the smallest NONZERO
+// eigenvalue (Ritz values under 1e-10 lmax are rounding-level null-space
+// components and are passed over).
+template <typename VT>
+static int lanczos_extremes(int64_t m, int64_t n, const int64_t *rp, const int32_t *col, const VT *val,
+                     int steps, uint64_t seed, cudaStream_t s, double *lmin, double *lmax)
+{
+    if (steps > n) steps = (int)n;
+    DevTmp t;
+    double *Q, *u, *y, *w, *h;
+    int st;
+    if ((st = t.alloc(&Q, (size_t)n * (steps + 1))) || (st = t.alloc(&u, (size_t)m)) ||
+        (st = t.alloc(&y, (size_t)m)) || (st = t.alloc(&w, (size_t)n)) ||
+        (st = t.alloc(&h, (size_t)steps + 1)))
+        return st;
+    double hb[2];
+    auto fetch = [&](int count) -> int {
+        ASYRK_CK(cudaMemcpyAsync(hb, h, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+        ASYRK_CK(cudaStreamSynchronize(s));
+        return ASYRK_OK;
+    };
+    const uint2 key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+    k_rand_sign<<<grid_for(m), 256, 0, s>>>(u, m, key);
+    ASYRK_CK(cudaMemsetAsync(w, 0, n * sizeof(double), s));
+    k_spmv_t<VT><<<grid_for(m), 256, 0, s>>>(m, rp, col, val, u, w);
+    k_dot_cols<<<1, 256, 0, s>>>(w, n, w, n, h);
+    ASYRK_CK(cudaGetLastError());
+    if ((st = fetch(1)) != ASYRK_OK) return st;
+    double beta = sqrt(hb[0]);
+    if (!(beta > 0.0)) return set_error(ASYRK_EINVAL, "A^T u = 0: the matrix has no nonzero entry");
+    k_scale_d<<<grid_for(n), 256, 0, s>>>(Q, w, 1.0 / beta, n);
+    std::vector<double> al, be(1, 0.0);
+    for (int j = 0; j < steps; ++j) {
+        double *qj = Q + (int64_t)j * n;
+        k_spmv<VT><<<grid_for(m), 256, 0, s>>>(m, rp, col, val, qj, y);
+        ASYRK_CK(cudaMemsetAsync(w, 0, n * sizeof(double), s));
+        k_spmv_t<VT><<<grid_for(m), 256, 0, s>>>(m, rp, col, val, y, w);
+        if (j > 0) k_axpy_d<<<grid_for(n), 256, 0, s>>>(w, qj - n, -be[j], n);
+        k_dot_cols<<<1, 256, 0, s>>>(qj, n, w, n, h);
+        ASYRK_CK(cudaGetLastError());
+        if ((st = fetch(1)) != ASYRK_OK) return st;
+        const double alpha = hb[0];
+        k_axpy_d<<<grid_for(n), 256, 0, s>>>(w, qj, -alpha, n);
+        for (int pass = 0; pass < 2; ++pass) {
+            k_dot_cols<<<j + 1, 256, 0, s>>>(Q, n, w, n, h);
+            k_sub_cols<<<grid_for(n), 256, 0, s>>>(w, Q, n, j + 1, h, n);
+        }
+        k_dot_cols<<<1, 256, 0, s>>>(w, n, w, n, h);
+        ASYRK_CK(cudaGetLastError());
+        if ((st = fetch(1)) != ASYRK_OK) return st;
+        al.push_back(alpha);
+        double amax = 0.0;
+        for (double a : al) amax = fmax(amax, fabs(a));
+        beta = sqrt(hb[0]);
+        if (!(beta > 1e-12 * amax) || j + 1 == steps) break;
+        be.push_back(beta);
+        k_scale_d<<<grid_for(n), 256, 0, s>>>(Q + (int64_t)(j + 1) * n, w, 1.0 / beta, n);
+    }
+    be.resize(al.size());
+    const int k = (int)al.size();
+    *lmax = tridiag_eig(al, be, k);
+    const int c0 = sturm_count(al, be, 1e-10 * *lmax);
+    if (c0 >= k) return set_error(ASYRK_EINVAL, "no nonzero Ritz value");
+    *lmin = tridiag_eig(al, be, c0 + 1);
+    return ASYRK_OK;
+}
+
+
+// A CSR matrix (and optionally b) on the device, copied there when the
+// caller's arrays are host arrays; row_ptr checked on the host.
+struct Csr {
+    int64_t m = 0, n = 0, nnz = 0;
+    const int64_t *rp = nullptr;
+    const int32_t *col = nullptr;
+    const void *val = nullptr;
+    const double *b = nullptr;
+};
+
+static int stage_csr(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                     const void *values, int vdtype, const double *b, bool on_dev, cudaStream_t s,
+                     DevTmp &t, Csr &c)
+{
+    std::vector<int64_t> rp((size_t)m + 1);
+    if (on_dev)
+        ASYRK_CK(cudaMemcpy(rp.data(), row_ptr, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    else
+        memcpy(rp.data(), row_ptr, (m + 1) * sizeof(int64_t));
+    if (rp[0] != 0) return set_error(ASYRK_EINVAL, "row_ptr[0] must be 0");
+    for (int64_t i = 0; i < m; ++i)
+        if (rp[i + 1] < rp[i] || rp[i + 1] - rp[i] > n)
+            return set_error(ASYRK_EINVAL, "row_ptr decreases or row %lld is longer than n",
+                             (long long)i);
+    c.m = m;
+    c.n = n;
+    c.nnz = rp[m];
+    if (c.nnz > 0xffffffffLL) return set_error(ASYRK_EINVAL, "more than 2^32-1 nonzeros");
+    c.rp = row_ptr;
+    c.col = col_idx;
+    c.val = values;
+    c.b = b;
+    if (on_dev) return ASYRK_OK;
+    const size_t es = dtype_size(vdtype);
+    int64_t *a;
+    int32_t *cc;
+    char *v;
+    double *bb = nullptr;
+    int st;
+    if ((st = t.alloc(&a, (size_t)m + 1)) || (st = t.alloc(&cc, (size_t)c.nnz)) ||
+        (st = t.alloc(&v, (size_t)c.nnz * es)) || (b && (st = t.alloc(&bb, (size_t)m))))
+        return st;
+    ASYRK_CK(cudaMemcpyAsync(a, rp.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    ASYRK_CK(cudaMemcpyAsync(cc, col_idx, c.nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    ASYRK_CK(cudaMemcpyAsync(v, values, c.nnz * es, cudaMemcpyHostToDevice, s));
+    if (b) ASYRK_CK(cudaMemcpyAsync(bb, b, m * sizeof(double), cudaMemcpyHostToDevice, s));
+    c.rp = a;
+    c.col = cc;
+    c.val = v;
+    c.b = bb;
+    return ASYRK_OK;
+}
+
+// Column range and order, finite values and b; fills the entry -> row map and
+// the column counts.
+template <typename VT>
+static int check_rows(const Csr &c, uint32_t *row_of, int64_t *ccount, unsigned *err,
+                      cudaStream_t s)
+{
+    ASYRK_CK(cudaMemsetAsync(ccount, 0, c.n * sizeof(int64_t), s));
+    ASYRK_CK(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+    k_lsq_rows<VT><<<grid_for(c.m), 256, 0, s>>>(c.m, c.n, c.rp, c.col, (const VT *)c.val, c.b,
+                                                 row_of, ccount, err);
+    ASYRK_CK(cudaGetLastError());
+    unsigned bad = 0;
+    ASYRK_CK(cudaMemcpyAsync(&bad, err, sizeof bad, cudaMemcpyDeviceToHost, s));
+    ASYRK_CK(cudaStreamSynchronize(s));
+    if (bad & BAD_COL) return set_error(ASYRK_EINVAL, "a column index is outside [0, n)");
+    if (bad & BAD_ORDER) return set_error(ASYRK_EINVAL, "column indices not strictly ascending in a row");
+    if (bad & BAD_VAL) return set_error(ASYRK_EINVAL, "a value is not finite");
+    if (bad & BAD_B) return set_error(ASYRK_EINVAL, "b is not finite");
+    return ASYRK_OK;
+}
+
+constexpr int DEFAULT_LANCZOS_STEPS = 100;
+
+template <typename VT>
+static int lsq_build(asyrk_problem **out, const Csr &c, int vdtype, const asyrk_lsq_opts &o,
+                     cudaStream_t s)
+{
+    const int64_t m = c.m, n = c.n, nnz = c.nnz;
+    const VT *val = (const VT *)c.val;
     const double phi = o.phi == 0.0 ? 1.0 : o.phi;
     DevTmp t;
     int st;
@@ -372,22 +623,24 @@ static int lsq_build(asyrk_problem **out, int64_t m, int64_t n, int64_t nnz,
         return st;
 
     // 1. checks, entry -> row map, column counts
-    ASYRK_CK(cudaMemsetAsync(ccount, 0, n * sizeof(int64_t), s));
-    ASYRK_CK(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
-    k_lsq_rows<VT><<<grid_for(m), 256, 0, s>>>(m, n, rp_d, col_d, val_d, b_d, row_of, ccount, err);
-    ASYRK_CK(cudaGetLastError());
-    unsigned bad = 0;
-    ASYRK_CK(cudaMemcpyAsync(&bad, err, sizeof bad, cudaMemcpyDeviceToHost, s));
-    ASYRK_CK(cudaStreamSynchronize(s));
-    if (bad & BAD_COL) return set_error(ASYRK_EINVAL, "a column index is outside [0, n)");
-    if (bad & BAD_ORDER) return set_error(ASYRK_EINVAL, "column indices not strictly ascending in a row");
-    if (bad & BAD_VAL) return set_error(ASYRK_EINVAL, "a value is not finite");
-    if (bad & BAD_B) return set_error(ASYRK_EINVAL, "b is not finite");
+    if ((st = check_rows<VT>(c, row_of, ccount, err, s)) != ASYRK_OK) return st;
 
-    // 2. entries sorted by column, stable, so rows ascend inside each column
+    // 2. zeta: the caller's, or Section 6's sigma_r / sqrt(2) with sigma_r^2 the
+    //    smallest nonzero Ritz value of A^T A
+    double zeta = o.zeta;
+    if (zeta == 0.0) {
+        double lmin = 0.0, lmax = 0.0;
+        const int steps = o.lanczos_steps > 0 ? o.lanczos_steps : DEFAULT_LANCZOS_STEPS;
+        if ((st = lanczos_extremes<VT>(m, n, c.rp, c.col, val, steps, o.seed, s, &lmin, &lmax)) !=
+            ASYRK_OK)
+            return st;
+        zeta = sqrt(0.5 * lmin);
+    }
+
+    // 3. entries sorted by column, stable, so rows ascend inside each column
     int cur = 0;
     if (nnz > 0) {
-        ASYRK_CK(cudaMemcpyAsync(keys[0], col_d, nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+        ASYRK_CK(cudaMemcpyAsync(keys[0], c.col, nnz * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
         k_iota_u32<<<grid_for(nnz), 256, 0, s>>>(perm[0], nnz);
         ASYRK_CK(cudaGetLastError());
         int bits = 0;
@@ -404,7 +657,7 @@ static int lsq_build(asyrk_problem **out, int64_t m, int64_t n, int64_t nnz,
         }
     }
 
-    // 3. column starts and the row number of each non-empty column
+    // 4. column starts and the row number of each non-empty column
     if ((st = exclusive_scan(ccount, cstart, n, scan_tmp, totals, s)) != ASYRK_OK) return st;
     k_nonempty<<<grid_for(n), 256, 0, s>>>(ccount, n, flag);
     ASYRK_CK(cudaGetLastError());
@@ -413,7 +666,7 @@ static int lsq_build(asyrk_problem **out, int64_t m, int64_t n, int64_t nnz,
     ASYRK_CK(cudaMemcpyAsync(&nne, totals + 1, sizeof nne, cudaMemcpyDeviceToHost, s));
     ASYRK_CK(cudaStreamSynchronize(s));
 
-    // 4. the system
+    // 5. the system
     const int64_t rows = nne + m, annz = 2 * nnz + m;
     int64_t *arp;
     int32_t *acol;
@@ -423,13 +676,13 @@ static int lsq_build(asyrk_problem **out, int64_t m, int64_t n, int64_t nnz,
         (st = t.alloc(&aval, (size_t)annz)) || (st = t.alloc(&ab, (size_t)rows)))
         return st;
     if (nnz > 0) {
-        k_lsq_first_block<VT><<<grid_for(nnz), 256, 0, s>>>(nnz, n, perm[cur], row_of, val_d, phi,
+        k_lsq_first_block<VT><<<grid_for(nnz), 256, 0, s>>>(nnz, n, perm[cur], row_of, val, phi,
                                                             acol, aval);
         k_lsq_rhs<VT><<<grid_for(n), 256, 0, s>>>(n, ccount, cstart, rowidx, perm[cur], row_of,
-                                                  val_d, b_d, phi, arp, ab);
+                                                  val, c.b, phi, arp, ab);
     }
-    k_lsq_second_block<VT><<<grid_for(m), 256, 0, s>>>(m, n, nne, nnz, rp_d, col_d, val_d, o.zeta,
-                                                       arp, acol, aval, ab);
+    k_lsq_second_block<VT><<<grid_for(m), 256, 0, s>>>(m, n, nne, nnz, c.rp, c.col, val, zeta, arp,
+                                                       acol, aval, ab);
     ASYRK_CK(cudaGetLastError());
     ASYRK_CK(cudaStreamSynchronize(s));
 
@@ -441,14 +694,42 @@ static int lsq_build(asyrk_problem **out, int64_t m, int64_t n, int64_t nnz,
     asyrk_problem *p = nullptr;
     if ((st = asyrk_create(&p, rows, n + m, arp, acol, aval, vdtype, ab, &co)) != ASYRK_OK) return st;
     p->lsq_n = n;
-    p->lsq_zeta = stored_value(vdtype, o.zeta);
+    p->lsq_zeta = stored_value(vdtype, zeta);
+    p->lsq_phi = phi;
     *out = p;
     return ASYRK_OK;
+}
+
+template <typename VT>
+static int spectrum_impl(const Csr &c, int steps, uint64_t seed, cudaStream_t s, double *lmin,
+                         double *lmax)
+{
+    DevTmp t;
+    uint32_t *row_of;
+    int64_t *ccount;
+    unsigned *err;
+    int st;
+    if ((st = t.alloc(&row_of, (size_t)c.nnz)) || (st = t.alloc(&ccount, (size_t)c.n)) ||
+        (st = t.alloc(&err, 1)))
+        return st;
+    if ((st = check_rows<VT>(c, row_of, ccount, err, s)) != ASYRK_OK) return st;
+    return lanczos_extremes<VT>(c.m, c.n, c.rp, c.col, (const VT *)c.val, steps, seed, s, lmin, lmax);
 }
 
 }  // namespace asyrk
 
 using namespace asyrk;
+
+static int check_dims(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                      const void *values, int vdtype)
+{
+    if (m <= 0 || n <= 0 || m + n > 0x7fffffffLL)
+        return set_error(ASYRK_EINVAL, "m, n >= 1 and m + n <= 2^31-1 required");
+    if (!row_ptr || !col_idx || !values) return set_error(ASYRK_EINVAL, "NULL array");
+    if (vdtype != ASYRK_F64 && vdtype != ASYRK_F32 && vdtype != ASYRK_BF16)
+        return set_error(ASYRK_EINVAL, "unknown value dtype %d", vdtype);
+    return ASYRK_OK;
+}
 
 extern "C" int asyrk_lsq_create(asyrk_problem **out, int64_t m, int64_t n, const int64_t *row_ptr,
                                 const int32_t *col_idx, const void *values, int vdtype,
@@ -456,62 +737,56 @@ extern "C" int asyrk_lsq_create(asyrk_problem **out, int64_t m, int64_t n, const
 {
     if (!out) return set_error(ASYRK_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!opts) return set_error(ASYRK_EINVAL, "opts is NULL (zeta has no default)");
+    if (!opts) return set_error(ASYRK_EINVAL, "opts is NULL");
     const asyrk_lsq_opts o = *opts;
-    if (m <= 0 || n <= 0 || m + n > 0x7fffffffLL)
-        return set_error(ASYRK_EINVAL, "m, n >= 1 and m + n <= 2^31-1 required");
-    if (!row_ptr || !col_idx || !values || !b) return set_error(ASYRK_EINVAL, "NULL array");
-    if (vdtype != ASYRK_F64 && vdtype != ASYRK_F32 && vdtype != ASYRK_BF16)
-        return set_error(ASYRK_EINVAL, "unknown value dtype %d", vdtype);
-    if (!(o.zeta > 0.0) || !isfinite(o.zeta)) return set_error(ASYRK_EINVAL, "zeta must be > 0");
+    int st = check_dims(m, n, row_ptr, col_idx, values, vdtype);
+    if (st != ASYRK_OK) return st;
+    if (!b) return set_error(ASYRK_EINVAL, "NULL b");
+    if (o.zeta < 0.0 || !isfinite(o.zeta)) return set_error(ASYRK_EINVAL, "zeta must be > 0 (0: estimated)");
     if (o.phi < 0.0 || !isfinite(o.phi)) return set_error(ASYRK_EINVAL, "phi must be > 0 (0: 1)");
-    if (o.reserved != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
+    if (o.lanczos_steps < 0) return set_error(ASYRK_EINVAL, "lanczos_steps < 0");
     cudaStream_t s = (cudaStream_t)o.stream;
-
-    std::vector<int64_t> rp((size_t)m + 1);
-    if (o.device_ptrs)
-        ASYRK_CK(cudaMemcpy(rp.data(), row_ptr, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
-    else
-        memcpy(rp.data(), row_ptr, (m + 1) * sizeof(int64_t));
-    if (rp[0] != 0) return set_error(ASYRK_EINVAL, "row_ptr[0] must be 0");
-    for (int64_t i = 0; i < m; ++i)
-        if (rp[i + 1] < rp[i] || rp[i + 1] - rp[i] > n)
-            return set_error(ASYRK_EINVAL, "row_ptr decreases or row %lld is longer than n",
-                             (long long)i);
-    const int64_t nnz = rp[m];
-    if (nnz > 0xffffffffLL) return set_error(ASYRK_EINVAL, "more than 2^32-1 nonzeros");
-
     DevTmp t;
-    const size_t es = dtype_size(vdtype);
-    const int64_t *rp_d = row_ptr;
-    const int32_t *col_d = col_idx;
-    const void *val_d = values;
-    const double *b_d = b;
-    if (!o.device_ptrs) {
-        int64_t *a;
-        int32_t *c;
-        char *v;
-        double *bb;
-        int st;
-        if ((st = t.alloc(&a, (size_t)m + 1)) || (st = t.alloc(&c, (size_t)nnz)) ||
-            (st = t.alloc(&v, (size_t)nnz * es)) || (st = t.alloc(&bb, (size_t)m)))
-            return st;
-        ASYRK_CK(cudaMemcpyAsync(a, rp.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        ASYRK_CK(cudaMemcpyAsync(c, col_idx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        ASYRK_CK(cudaMemcpyAsync(v, values, nnz * es, cudaMemcpyHostToDevice, s));
-        ASYRK_CK(cudaMemcpyAsync(bb, b, m * sizeof(double), cudaMemcpyHostToDevice, s));
-        rp_d = a;
-        col_d = c;
-        val_d = v;
-        b_d = bb;
-    }
+    Csr c;
+    if ((st = stage_csr(m, n, row_ptr, col_idx, values, vdtype, b, o.device_ptrs != 0, s, t, c)) !=
+        ASYRK_OK)
+        return st;
     switch (vdtype) {
-    case ASYRK_F64:
-        return lsq_build<double>(out, m, n, nnz, rp_d, col_d, (const double *)val_d, b_d, vdtype, o, s);
-    case ASYRK_F32:
-        return lsq_build<float>(out, m, n, nnz, rp_d, col_d, (const float *)val_d, b_d, vdtype, o, s);
-    default:
-        return lsq_build<bf16_t>(out, m, n, nnz, rp_d, col_d, (const bf16_t *)val_d, b_d, vdtype, o, s);
+    case ASYRK_F64: return lsq_build<double>(out, c, vdtype, o, s);
+    case ASYRK_F32: return lsq_build<float>(out, c, vdtype, o, s);
+    default: return lsq_build<bf16_t>(out, c, vdtype, o, s);
+    }
+}
+
+extern "C" int asyrk_lsq_params(const asyrk_problem *p, double *zeta, double *phi)
+{
+    if (!p) return set_error(ASYRK_EINVAL, "NULL problem");
+    if (p->lsq_n <= 0) return set_error(ASYRK_EINVAL, "not a least-squares problem");
+    if (zeta) *zeta = p->lsq_zeta;
+    if (phi) *phi = p->lsq_phi;
+    return ASYRK_OK;
+}
+
+extern "C" int asyrk_spectrum_estimate(int64_t m, int64_t n, const int64_t *row_ptr,
+                                       const int32_t *col_idx, const void *values, int vdtype,
+                                       int device_ptrs, int32_t steps, uint64_t seed,
+                                       void *stream, double *lambda_min, double *lambda_max)
+{
+    int st = check_dims(m, n, row_ptr, col_idx, values, vdtype);
+    if (st != ASYRK_OK) return st;
+    if (!lambda_min || !lambda_max) return set_error(ASYRK_EINVAL, "NULL output");
+    if (steps < 0) return set_error(ASYRK_EINVAL, "steps < 0");
+    if (steps == 0) steps = DEFAULT_LANCZOS_STEPS;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevTmp t;
+    Csr c;
+    if ((st = stage_csr(m, n, row_ptr, col_idx, values, vdtype, nullptr, device_ptrs != 0, s, t,
+                        c)) != ASYRK_OK)
+        return st;
+    switch (vdtype) {
+    case ASYRK_F64: return spectrum_impl<double>(c, steps, seed, s, lambda_min, lambda_max);
+    case ASYRK_F32: return spectrum_impl<float>(c, steps, seed, s, lambda_min, lambda_max);
+    default: return spectrum_impl<bf16_t>(c, steps, seed, s, lambda_min, lambda_max);
     }
 }
 

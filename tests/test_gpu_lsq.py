@@ -9,6 +9,9 @@
     values to 1e-8, FP32 values with FP64 refinement to 1e-9;
   * a large inconsistent system (m = 200000, n = 50000, Section 5's random
     positions) reaches ||A^T(A x - b)|| <= 1e-6 ||A^T b||, re-measured on the host;
+  * the GPU Lanczos estimate of lambda_min (nonzero) and lambda_max of A^T A
+    lies inside the spectrum and reaches its ends (numpy SVD), skipping the
+    null space of a rank-deficient A; zeta = 0 takes sigma_r/sqrt(2) from it;
   * bad arguments are refused.
 """
 import numpy as np
@@ -136,11 +139,63 @@ def test_large_inconsistent_system_reaches_normal_equations():
     assert np.linalg.norm(gr) <= 1e-6 * np.linalg.norm(atb)
 
 
+@pytest.mark.parametrize("m,n,dtype", [(3000, 1000, "f64"), (1000, 300, "f32"),
+                                       (2000, 1500, "bf16")])
+def test_spectrum_estimate_lies_inside_and_converges(m, n, dtype):
+    s = synth.make_system(m, n, 10, 31, row_norms="unit", value_dtype=dtype)
+    sv = np.linalg.svd(oracle.dense(m, n, s.row_ptr, s.col, s.val64), compute_uv=False)
+    st, lmin, lmax = asyrk.asyrk_spectrum_estimate(m, n, s.row_ptr, s.col, s.val_store,
+                                                   asyrk.DTYPES[dtype], steps=200, seed=4)
+    assert st == asyrk.OK
+    # Ritz values lie inside the spectrum (Cauchy interlacing) ...
+    assert lmin >= (1 - 1e-9) * sv.min() ** 2 and lmax <= (1 + 1e-9) * sv.max() ** 2
+    # ... and after 200 steps sit at its ends
+    assert lmin <= 1.01 * sv.min() ** 2 and lmax >= (1 - 1e-9) * sv.max() ** 2
+
+
+def test_spectrum_estimate_skips_the_null_space():
+    m, n = 1000, 300
+    s = synth.make_system(m, n, 8, 9, row_norms="unit", value_dtype="f64")
+    A = oracle.dense(m, n, s.row_ptr, s.col, s.val64)
+    A[:, 5] = A[:, 9]  # rank n - 1; rows stay non-empty
+    rp = np.zeros(m + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(np.count_nonzero(A, axis=1))
+    rows, cols = np.nonzero(A)
+    sv = np.linalg.svd(A, compute_uv=False)
+    sr = sv[sv > 1e-10 * sv[0]].min()
+    assert sv.min() < 1e-12
+    st, lmin, lmax = asyrk.asyrk_spectrum_estimate(m, n, rp, cols.astype(np.int32), A[rows, cols],
+                                                   asyrk.F64, steps=100)
+    assert st == asyrk.OK
+    assert (1 - 1e-9) * sr ** 2 <= lmin <= 1.01 * sr ** 2
+
+
+def test_estimated_zeta_and_least_squares():
+    s, b, A, x_ls, sr = _inconsistent(3000, 1000, 12, 73, "f64")
+    with asyrk.Problem.lsq(s.m, s.n, s.row_ptr, s.col, s.val_store, "f64", b, seed=9) as p:
+        zeta, phi = p.lsq_params()
+        assert phi == 1.0
+        assert sr / np.sqrt(2) * (1 - 1e-9) <= zeta <= 1.005 * sr / np.sqrt(2)
+        z = np.zeros(s.n + s.m)
+        st, info = p.solve(z, tol=1e-11, max_sweeps=4000)
+        assert st == asyrk.OK, info.as_dict()
+        x = p.lsq_solution(z)
+    assert np.linalg.norm(x - x_ls) <= 1e-8 * np.linalg.norm(x_ls)
+
+
 def test_bad_arguments_are_refused():
     m, n, rp, col, v64, store, b = _with_gaps("f64")
-    for zeta, phi in [(0.0, 1.0), (-1.0, 1.0), (np.inf, 1.0), (0.5, -1.0), (0.5, np.nan)]:
+    for zeta, phi in [(-1.0, 1.0), (np.inf, 1.0), (0.5, -1.0), (0.5, np.nan)]:
         st, h = asyrk.asyrk_lsq_create(m, n, rp, col, store, asyrk.F64, b, zeta, phi=phi)
         assert st == asyrk.EINVAL and not h.value
+    st, h = asyrk.asyrk_lsq_create(m, n, rp, col, store, asyrk.F64, b, 0.0, lanczos_steps=-1)
+    assert st == asyrk.EINVAL and not h.value
+    st, lo, hi = asyrk.asyrk_spectrum_estimate(m, n, rp, col, store, asyrk.F64, steps=-1)
+    assert st == asyrk.EINVAL
+    bad_sp = col.copy()
+    bad_sp[0] = -1
+    st, lo, hi = asyrk.asyrk_spectrum_estimate(m, n, rp, bad_sp, store, asyrk.F64)
+    assert st == asyrk.EINVAL
     bad = col.copy()
     bad[5] = n
     st, h = asyrk.asyrk_lsq_create(m, n, rp, bad, store, asyrk.F64, b, 0.5)
