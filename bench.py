@@ -399,6 +399,43 @@ def extras_table2(asyrk, synth, torch):
             "rows": rows}
 
 
+def extras_tau_study(asyrk, synth, torch):
+    """Figures 1-2 on the GPU: m=80000, n=100000, delta = 0.001 and 0.003, gamma = 1;
+    epochs (n projections) to ||Ax - b||/||b|| <= 1e-4 and time, for a range of worker
+    counts W (the delay tau grows with W, and with row density under full-row
+    updates, Section 5); speedup against the smallest W's time."""
+    out = []
+    for k, delta in enumerate((0.001, 0.003)):
+        m, n = 80000, 100000
+        d = synth.make_system_torch(m, n, ("poisson", delta * n), 7100 + k, row_norms="unit",
+                                    value_dtype="f32")
+        torch.cuda.synchronize()
+        p = asyrk.Problem(m, n, d["row_ptr"], d["col"], d["val_store"], asyrk.F32, d["b"],
+                          seed=synth.solver_seed(7100 + k), device_ptrs=True)
+        del d
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        rows = []
+        for W in (32, 128, 512, 2048, 8192, 32768, 0):
+            x.zero_()
+            p.position = 0
+            torch.cuda.synchronize()
+            st, info = p.solve(x, tol=1e-4, max_sweeps=3000, workers=W, device_ptrs=True,
+                               measure=asyrk.MEASURE_RESIDUAL, sampling=asyrk.SAMPLE_SHUFFLED)
+            rows.append({"workers": info.workers, "status": st, "ms": 1e3 * info.seconds,
+                         "epochs_n_iterations": info.projections / n,
+                         "skipped_fraction": info.skipped / max(1, info.projections + info.skipped),
+                         "projections_per_s": info.projections / info.seconds})
+        p.close()
+        t0 = rows[0]["ms"]
+        for r in rows:
+            r["speedup_vs_fewest_workers"] = t0 / r["ms"]
+        out.append({"delta": delta, "rows": rows})
+    return {"workload": "Figures 1-2 shapes: m=80000, n=100000, Section 5's generator (unit rows, "
+                        "Poisson(delta n) per row), FP32, gamma=1, shuffled sweeps as in the "
+                        "paper's implementation; stop ||Ax-b||/||b|| <= 1e-4; workers=0 is the "
+                        "automatic count", "deltas": out}
+
+
 def extras_lsq(asyrk, synth, torch):
     """Section 6: least squares of an inconsistent system through the square
     consistent system [[0, A^T], [A, -zeta I]] (phi = 1), built on the GPU,
@@ -700,14 +737,21 @@ def run_asyrk(args, dist):
                                      pin(s.x_true))
     h_x = torch.zeros(s.n, dtype=torch.float64).pin_memory()
     e2e_t, e2e_proj = 0.0, 0
+    split = {"create_s": 0.0, "solve_s": 0.0, "destroy_s": 0.0}
     for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):  # first round warms up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with asyrk.Problem(s.m, s.n, h_rp, h_col, h_val, asyrk.F32, h_b, seed=seed) as q:
+            t1 = time.perf_counter()
             h_x.zero_()
             st, info = q.solve(h_x, gamma=args.gamma, tol=args.tol, max_sweeps=max_sweeps,
                                x_true=h_xt)
+            t2 = time.perf_counter()
         dt = time.perf_counter() - t0
+        if k > 0:
+            split["create_s"] += t1 - t0
+            split["solve_s"] += t2 - t1
+            split["destroy_s"] += t0 + dt - t2
         if st != asyrk.OK:
             raise RuntimeError("e2e solve status %d" % st)
         if k > 0:
@@ -720,7 +764,8 @@ def run_asyrk(args, dist):
     d2h = 2 * 8 * s.m + 8 * s.n  # row weights and b back for the alias table, x
     e2e = None if args.e2e_steps <= 0 else {"value": e2e_proj / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h),
-           "what": "asyrk_create from pinned host CSR + asyrk_solve (host x0 -> host x) + destroy"}
+           "what": "asyrk_create from pinned host CSR + asyrk_solve (host x0 -> host x) + destroy",
+           "ms_per_step_split": {k: 1e3 * v / max(1, args.e2e_steps) for k, v in split.items()}}
 
     cpu = None
     cpu_mt = None
@@ -736,6 +781,7 @@ def run_asyrk(args, dist):
         extras = {"plain_and_refine": extras_plain_refine(asyrk, synth),
                   "table2": extras_table2(asyrk, synth, torch),
                   "least_squares": extras_lsq(asyrk, synth, torch),
+                  "tau_study": extras_tau_study(asyrk, synth, torch),
                   "batched": extras_batched(asyrk, synth, torch),
                   "served": extras_served(asyrk, synth, torch, args.served_seconds,
                                           args.served_rate)}
