@@ -11,8 +11,10 @@
 
 namespace asyrk {
 
+// 5 blocks of 256 per SM (<= 48 registers) with an FP32 iterate and G > 1; 4
+// (<= 64) with FP64 values in flight or one lane walking a whole row
 template <typename VT, typename XT, int G, bool SEQ, bool EXCL>
-__global__ void __launch_bounds__(256, 4) k_project(const ProjArgs a)  // <= 64 registers
+__global__ void __launch_bounds__(256, (sizeof(XT) == 4 && G > 1 ? 5 : 4)) k_project(const ProjArgs a)
 {
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long skipped = run_workers<VT, XT, G, SEQ, EXCL>(a, warp * (32 / G),

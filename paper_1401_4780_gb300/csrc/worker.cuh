@@ -152,7 +152,8 @@ __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, lon
                                                           long long W)
 {
     constexpr int GPW = 32 / G;  // workers per warp
-    constexpr int CH = 2;        // row chunks of 4G entries kept in registers
+    constexpr int CH = 1;        // row chunks of 4G entries kept in registers (longer rows
+                                 // re-read their tail for the scatter)
     constexpr bool F64 = std::is_same<XT, double>::value;
     const int lane = threadIdx.x & 31;
     const int sub = lane / G, sl = lane % G;
