@@ -35,8 +35,20 @@
  *     its row from Philox4x32-10 (Salmon et al., SC'11) with key = seed and
  *     counter = (j mod 2^32, j div 2^32, stream id, 0): bucket =
  *     floor(u0 * m / 2^32); row = bucket if u1 < thr[bucket] else
- *     alias[bucket], where (thr, alias) is Vose's alias table of the row
- *     weights ||a_i||^2 (unused when all weights are bit-identical).
+ *     alias[bucket], where (thr, alias) is the alias table (Walker's method)
+ *     of the row weights w_i = ||a_i||^2 (unused when all weights are
+ *     bit-identical), built on the GPU and defined by one sweep:
+ *     F = ||A||_F^2 sums blocks of 2048 consecutive w_i in index order, then
+ *     the block sums in order; integer masses M_i = floor(((w_i m) / F) 2^32)
+ *     (one bucket is U = 2^32 units), the D = m U - sum M_i units lost to the
+ *     floors added one per row from row 0 on (D / m to every row first when
+ *     D >= m), an overshoot (D < 0) taken off the first row of largest mass;
+ *     lights (M < U) and heavies (M >= U) each in index order; every light l
+ *     in turn gets thr = M_l and alias = the heavy being drawn down, whose
+ *     residual drops by U - M_l; while that residual R is below U the heavy
+ *     gets thr = R, alias = the next heavy, and the next heavy's residual is
+ *     its mass minus (U - R); the last heavy and heavies never drawn below U
+ *     keep thr = 2^32 - 1 and alias = themselves.
  */
 #ifndef ASYRK_H
 #define ASYRK_H

@@ -161,7 +161,8 @@ def row_weights(m, row_ptr, val):
 
 
 def alias_table(w, F):
-    """Vose alias table (thr, alias, uniform) for probabilities w_i / F."""
+    """Alias table (thr, alias, uniform) for probabilities w_i / F (the sweep over
+    integer masses stated in asyrk_oracle.c)."""
     w = np.ascontiguousarray(w, dtype=np.float64)
     m = w.shape[0]
     thr = np.zeros(m, dtype=np.uint32)

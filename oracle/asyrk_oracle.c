@@ -26,15 +26,27 @@
  *   bucket = floor(u0 * m / 2^32);  i = (u1 < thr[bucket]) ? bucket
  *                                                         : alias[bucket]
  * with Philox4x32-10 written from Salmon, Moraes, Dror and Shaw, "Parallel
- * random numbers: as easy as 1, 2, 3" (SC'11), and the alias table built by
- * Vose's method on q_i = w_i m / F (w_i = ||a_i||^2, F = ||A||_F^2):
- *   - "small" (q < 1) and "large" (q >= 1) are filled in ascending i and
- *     used as stacks (last in, first out);
- *   - while both are non-empty: s = top of small (popped), l = top of large;
- *     thr[s] = min(floor(q_s 2^32), 2^32 - 1), alias[s] = l,
- *     q_l <- (q_l + q_s) - 1; if q_l < 1, l moves from large to small;
- *   - every entry left in either stack gets thr = 2^32 - 1, alias = itself;
+ * random numbers: as easy as 1, 2, 3" (SC'11), and an alias table (Walker's
+ * method) built as follows:
+ *   - F = ||A||_F^2 is summed in blocks of 2048 consecutive rows (each block in
+ *     index order, then the block sums in order);
+ *   - integer masses M_i = floor(((w_i m) / F) 2^32) (FP64, in that order);
+ *     one bucket holds U = 2^32; the D = m U - sum M_i units the floors lose
+ *     go one per row from row 0 on (D/m to every row first when D >= m), and
+ *     an overshoot (D < 0) comes off the first row of largest mass, so the
+ *     masses add up to m U exactly;
+ *   - lights (M_i < U) and heavies (M_i >= U), each list in index order;
+ *   - one sweep over the lights: light l gets thr = M_l and alias = the heavy
+ *     being drawn down, whose residual (initially its mass) drops by U - M_l;
+ *     while that residual R is below U, the heavy gets thr = R and alias = the
+ *     next heavy, whose residual becomes its mass minus (U - R); the last
+ *     heavy and heavies never drawn below U keep thr = 2^32 - 1, alias =
+ *     themselves (with exact masses no light is left without a heavy);
  *   - if all w_i are bit-identical, the table is skipped and i = bucket.
+ * This sweep is equivalent to a form the GPU evaluates in parallel: with
+ * S_k the deficit U - M of the lights before light k and C_t the excess
+ * M - U of heavies 0..t, light k pairs with heavy #{t : C_t < S_k} and heavy t
+ * falls below U just after the first light k with S_{k+1} > C_t.
  *
  * Shuffled sweeps (the paper's implementation visits rows without
  * replacement, reshuffled after each scan, Section 5): projection j belongs to
@@ -65,6 +77,8 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+
+#define ORACLE_F_BLOCK 2048
 
 #define OR_OK 0
 #define OR_EINVAL (-1)
@@ -137,48 +151,83 @@ int oracle_validate(int64_t m, int64_t n, const int64_t *row_ptr,
 double oracle_row_weights(int64_t m, const int64_t *row_ptr, const double *val,
                           double *w)
 {
-    double F = 0.0;
     for (int64_t i = 0; i < m; ++i) {
         double s = 0.0;
         for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += val[k] * val[k];
         w[i] = s;
-        F += s;
+    }
+    /* F: the sum of each block of ORACLE_F_BLOCK consecutive w_i in index
+     * order, then the block sums in block order */
+    double F = 0.0;
+    for (int64_t b0 = 0; b0 < m; b0 += ORACLE_F_BLOCK) {
+        const int64_t b1 = b0 + ORACLE_F_BLOCK < m ? b0 + ORACLE_F_BLOCK : m;
+        double part = 0.0;
+        for (int64_t i = b0; i < b1; ++i) part += w[i];
+        F += part;
     }
     return F;
 }
 
-/* Vose's alias table; returns 1 when all weights are bit-identical (the
- * table is then unused and left as the identity), 0 otherwise, or
- * OR_ENOMEM. */
+/* The alias table (see the header): integer masses M_i = floor(q_i 2^32) with
+ * q_i = (w_i m) / F, lights (M < 2^32) and heavies (M >= 2^32) each in index
+ * order, and one sweep that hands each light the heavy currently being drawn
+ * down; a heavy whose residual falls below 2^32 keeps that residual as its
+ * threshold and hands the rest to the next heavy.  Returns 1 when all
+ * weights are bit-identical (the table is then unused and left as the
+ * identity), 0 otherwise, or OR_ENOMEM. */
 int oracle_alias_build(int64_t m, const double *w, double F, uint32_t *thr,
                        uint32_t *alias)
 {
+    const int64_t U = (int64_t)1 << 32;
     int all_equal = 1;
     for (int64_t i = 1; i < m; ++i)
         if (memcmp(&w[i], &w[0], sizeof(double)) != 0) { all_equal = 0; break; }
     for (int64_t i = 0; i < m; ++i) { thr[i] = 0xffffffffu; alias[i] = (uint32_t)i; }
     if (all_equal) return 1;
 
-    double *q = (double *)malloc((size_t)m * sizeof(double));
-    int64_t *small = (int64_t *)malloc((size_t)m * sizeof(int64_t));
-    int64_t *large = (int64_t *)malloc((size_t)m * sizeof(int64_t));
-    if (!q || !small || !large) { free(q); free(small); free(large); return OR_ENOMEM; }
-    int64_t ns = 0, nl = 0;
+    int64_t *M = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    int64_t *light = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    int64_t *heavy = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    if (!M || !light || !heavy) { free(M); free(light); free(heavy); return OR_ENOMEM; }
+    int64_t L = 0, H = 0, sum = 0;
     for (int64_t i = 0; i < m; ++i) {
-        q[i] = (w[i] * (double)m) / F;
-        if (q[i] < 1.0) small[ns++] = i; else large[nl++] = i;
+        const double q = (w[i] * (double)m) / F;
+        M[i] = (int64_t)floor(q * 4294967296.0);
+        sum += M[i];
     }
-    while (ns > 0 && nl > 0) {
-        int64_t s = small[--ns];
-        int64_t l = large[nl - 1];
-        double t = floor(q[s] * 4294967296.0);
-        thr[s] = (t >= 4294967295.0) ? 0xffffffffu : (uint32_t)t;
-        alias[s] = (uint32_t)l;
-        q[l] = (q[l] + q[s]) - 1.0;
-        if (q[l] < 1.0) { --nl; small[ns++] = l; }
+    /* the masses must add up to m buckets: D = m U - sum units are added one
+     * per row from row 0 on (D / m to every row first if D >= m), or, when the
+     * rounding overshoots (D < 0), taken from the first row of largest mass */
+    const int64_t D = m * U - sum;
+    if (D >= 0) {
+        for (int64_t i = 0; i < m; ++i) M[i] += D / m + (i < D % m ? 1 : 0);
+    } else {
+        int64_t a = 0;
+        for (int64_t i = 1; i < m; ++i) if (M[i] > M[a]) a = i;
+        M[a] += D;
     }
-    /* whatever remains keeps thr = 2^32-1, alias = self */
-    free(q); free(small); free(large);
+    for (int64_t i = 0; i < m; ++i) {
+        if (M[i] < U) light[L++] = i; else heavy[H++] = i;
+    }
+    int64_t t = 0;                  /* the heavy being drawn down */
+    int64_t R = H > 0 ? M[heavy[0]] : 0;  /* its residual mass */
+    for (int64_t k = 0; k < L; ++k) {
+        const int64_t l = light[k];
+        if (t >= H) break;          /* no heavy left: l keeps thr = max, alias = l */
+        thr[l] = (uint32_t)M[l];
+        alias[l] = (uint32_t)heavy[t];
+        R -= U - M[l];
+        while (t < H && R < U) {    /* heavy[t] is drawn below one bucket */
+            const int64_t h = heavy[t];
+            if (t + 1 < H) {
+                thr[h] = (uint32_t)R;
+                alias[h] = (uint32_t)heavy[t + 1];
+                R = M[heavy[t + 1]] - (U - R);
+            }
+            ++t;                    /* the last heavy keeps thr = max, alias = itself */
+        }
+    }
+    free(M); free(light); free(heavy);
     return 0;
 }
 

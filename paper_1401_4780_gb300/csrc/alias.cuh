@@ -1,0 +1,16 @@
+// alias.cuh -- row totals and the alias table on the GPU (alias.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace asyrk {
+
+// From p->w64 and p->b64 (filled by the row pass): p->frob2 = F (blocks of 2048
+// rows in index order, then the block sums), p->bnorm, p->uniform, and, when
+// the weights are not all bit-identical, the alias thresholds and rows in
+// p->rec (whose thr/alias the row pass set to 2^32 - 1 / the row itself).
+// Synchronises the stream.  Errors: EINVAL (F not positive and finite),
+// ENOMEM, ECUDA.
+int row_totals_and_alias(asyrk_problem *p, cudaStream_t s);
+
+}  // namespace asyrk

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "scan.cuh"
 
 namespace asyrk {
 
@@ -27,7 +28,6 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;  // keys per thread; a warp owns 8 rounds of 32 consecutive keys
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SCAN_TILE = 2048;
 
 __device__ __forceinline__ double widen_v(double v) { return v; }
 __device__ __forceinline__ double widen_v(float v) { return (double)v; }
@@ -45,78 +45,6 @@ __device__ __forceinline__ void narrow_v(double d, bf16_t &v)
 }
 
 enum : unsigned { BAD_COL = 1u, BAD_ORDER = 2u, BAD_VAL = 4u, BAD_B = 8u };
-
-// ---- device-wide exclusive scan of int64 (three passes) -------------------
-__global__ void k_scan_tiles(const int64_t *__restrict__ in, int64_t *__restrict__ out,
-                             int64_t *__restrict__ tile_sum, int64_t count)
-{
-    __shared__ int64_t part[SCAN_TILE / 8];
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    const int t = threadIdx.x;  // 256 threads, 8 items each
-    int64_t v[8], run = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int64_t q = base + t * 8 + k;
-        v[k] = q < count ? in[q] : 0;
-        run += v[k];
-    }
-    part[t] = run;
-    __syncthreads();
-    if (t == 0) {
-        int64_t acc = 0;
-        for (int w = 0; w < SCAN_TILE / 8; ++w) {
-            const int64_t x = part[w];
-            part[w] = acc;
-            acc += x;
-        }
-        tile_sum[blockIdx.x] = acc;
-    }
-    __syncthreads();
-    int64_t acc = part[t];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int64_t q = base + t * 8 + k;
-        if (q < count) out[q] = acc;
-        acc += v[k];
-    }
-}
-
-__global__ void k_scan_sums(int64_t *__restrict__ tile_sum, int64_t tiles, int64_t *__restrict__ total)
-{
-    // one thread: tile counts are small (count / 2048)
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t acc = 0;
-    for (int64_t k = 0; k < tiles; ++k) {
-        const int64_t x = tile_sum[k];
-        tile_sum[k] = acc;
-        acc += x;
-    }
-    *total = acc;
-}
-
-__global__ void k_scan_add(int64_t *__restrict__ out, const int64_t *__restrict__ tile_sum,
-                           int64_t count)
-{
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < count) out[q] += tile_sum[q / SCAN_TILE];
-}
-
-// out[0..count) = exclusive scan of in; *total = the sum.  tmp holds
-// ceil(count / SCAN_TILE) entries.
-int exclusive_scan(const int64_t *in, int64_t *out, int64_t count, int64_t *tmp, int64_t *total,
-                   cudaStream_t s)
-{
-    const int64_t tiles = (count + SCAN_TILE - 1) / SCAN_TILE;
-    if (tiles == 0) {
-        ASYRK_CK(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
-        return ASYRK_OK;
-    }
-    k_scan_tiles<<<(unsigned)tiles, 256, 0, s>>>(in, out, tmp, count);
-    k_scan_sums<<<1, 32, 0, s>>>(tmp, tiles, total);
-    k_scan_add<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, tmp, count);
-    ASYRK_CK(cudaGetLastError());
-    return ASYRK_OK;
-}
 
 // ---- stable LSD radix sort of (key, value) by 8-bit digits ----------------
 // Tile t holds keys [t*SORT_TILE, (t+1)*SORT_TILE); inside it warp w holds
@@ -618,7 +546,7 @@ static int lsq_build(asyrk_problem **out, const Csr &c, int vdtype, const asyrk_
         (st = t.alloc(&cstart, (size_t)n)) || (st = t.alloc(&flag, (size_t)n)) ||
         (st = t.alloc(&rowidx, (size_t)n)) || (st = t.alloc(&hist, (size_t)(256 * tiles))) ||
         (st = t.alloc(&offs, (size_t)(256 * tiles))) ||
-        (st = t.alloc(&scan_tmp, (size_t)(scan_max / SCAN_TILE + 1))) ||
+        (st = t.alloc(&scan_tmp, (size_t)scan_tmp_count(scan_max))) ||
         (st = t.alloc(&totals, 2)) || (st = t.alloc(&err, 1)))
         return st;
 

@@ -2,14 +2,16 @@
 //
 // Set-up of a problem (Section 1 of the paper: A x = b consistent, no zero
 // rows; rows are drawn with probability ||a_i||^2/||A||_F^2):
-//   1. row_ptr is checked on the host and the padded row starts (rounded up
-//      to 4 entries) are computed;
+//   1. a GPU pass over row_ptr checks it (rp[0] = 0, no empty row, no row
+//      longer than n) and a prefix sum gives the padded row starts (rows
+//      rounded up to 4 entries);
 //   2. a GPU pass over the rows checks columns (strictly ascending, in range)
 //      and values (finite), computes w_i = ||a_i||^2 in FP64 in CSR order
 //      without fused multiply-adds, and writes the row records and the
 //      padded column/value arrays;
-//   3. the host builds Vose's alias table of the w_i (the same specification
-//      as documented in asyrk.h) and the GPU merges it into the records.
+//   3. ||A||_F^2, ||b|| and the alias table of the w_i (as specified in
+//      asyrk.h) are computed on the GPU (alias.cu) and written into the
+//      records.  The host only reads back sizes, flags and the totals.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -17,7 +19,9 @@
 
 #include <vector>
 
+#include "alias.cuh"
 #include "common.cuh"
+#include "scan.cuh"
 
 namespace asyrk {
 
@@ -136,52 +140,6 @@ __global__ void k_row_setup(int64_t m, int64_t n, const int64_t *__restrict__ ro
     b64[i] = bi;
 }
 
-__global__ void k_set_alias(int64_t m, const uint2 *__restrict__ tab, RowRec *__restrict__ rec)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const uint2 t = tab[i];
-    rec[i].thr = t.x;
-    rec[i].alias = t.y;
-}
-
-// Vose's method, in the order stated in asyrk.h: q_i = w_i m / F; "small"
-// (q < 1) and "large" (q >= 1) stacks filled in ascending i; pair the top of
-// small with the top of large; the large entry's q absorbs the deficit and
-// moves to small once below 1; leftovers keep thr = 2^32-1 and themselves.
-// Returns true when all weights are bit-identical (no table needed).
-static bool build_alias(const std::vector<double> &w, double F, std::vector<uint2> &tab)
-{
-    const size_t m = w.size();
-    tab.resize(m);
-    for (size_t i = 0; i < m; ++i) tab[i] = make_uint2(0xffffffffu, (unsigned)i);
-    bool same = true;
-    for (size_t i = 1; i < m && same; ++i) same = (memcmp(&w[i], &w[0], sizeof(double)) == 0);
-    if (same) return true;
-    std::vector<double> q(m);
-    std::vector<size_t> small, large;
-    small.reserve(m);
-    large.reserve(m);
-    const double md = (double)m;
-    for (size_t i = 0; i < m; ++i) {
-        q[i] = (w[i] * md) / F;
-        (q[i] < 1.0 ? small : large).push_back(i);
-    }
-    while (!small.empty() && !large.empty()) {
-        const size_t s = small.back();
-        small.pop_back();
-        const size_t l = large.back();
-        const double scaled = floor(q[s] * 4294967296.0);
-        tab[s].x = scaled >= 4294967295.0 ? 0xffffffffu : (unsigned)scaled;
-        tab[s].y = (unsigned)l;
-        q[l] = (q[l] + q[s]) - 1.0;
-        if (q[l] < 1.0) {
-            large.pop_back();
-            small.push_back(l);
-        }
-    }
-    return false;
-}
 
 static size_t value_size(int dtype)
 {
@@ -255,6 +213,31 @@ static void free_problem(asyrk_problem *p)
     delete p;
 }
 
+// Row-pointer pass: rp[0] = 0, every row non-empty and at most n long; the
+// padded length of each row (a multiple of 4 entries) and the row lengths'
+// maximum; whether every row already starts at a multiple of 4.
+enum : unsigned { RP_FIRST = 1u, RP_EMPTY = 2u, RP_LONG = 4u, RP_MISALIGNED = 8u };
+
+__global__ void k_rowptr_pass(int64_t m, int64_t n, const int64_t *__restrict__ rp,
+                              int64_t *__restrict__ plen, unsigned long long *__restrict__ info)
+{
+    // info[0]: flags, info[1]: max row length, info[2]: first bad row
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t s = rp[i], len = rp[i + 1] - s;
+    unsigned f = 0;
+    if (i == 0 && s != 0) f |= RP_FIRST;
+    if (len <= 0) f |= RP_EMPTY;
+    if (len > n) f |= RP_LONG;
+    if (s & 3) f |= RP_MISALIGNED;
+    plen[i] = len > 0 ? ((len + 3) & ~(int64_t)3) : 0;
+    if (len > 0) atomicMax(&info[1], (unsigned long long)len);
+    if (f) {
+        atomicOr(&info[0], (unsigned long long)f);
+        if (f & (RP_FIRST | RP_EMPTY | RP_LONG)) atomicMin(&info[2], (unsigned long long)i);
+    }
+}
+
 static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *col_idx,
                        const void *values, const double *b, const asyrk_create_opts *o)
 {
@@ -264,51 +247,18 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
     ASYRK_CK(cudaGetDevice(&p->device));
     ASYRK_CK(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
 
-    // 1. row pointers on the host: monotone, no zero rows, padded starts
-    std::vector<int64_t> rp((size_t)m + 1);
-    if (on_dev)
-        ASYRK_CK(cudaMemcpy(rp.data(), row_ptr, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
-    else
-        memcpy(rp.data(), row_ptr, (m + 1) * sizeof(int64_t));
-    if (rp[0] != 0) return set_error(ASYRK_EINVAL, "row_ptr[0] = %lld, expected 0", (long long)rp[0]);
-    bool aligned = true;
-    int64_t max_len = 0, pad_total = 0;
-    std::vector<int64_t> pstart((size_t)m);
-    for (int64_t i = 0; i < m; ++i) {
-        const int64_t len = rp[i + 1] - rp[i];
-        if (len <= 0)
-            return set_error(ASYRK_EINVAL, "row %lld is empty or row_ptr decreases (the problem "
-                             "has no zero rows)", (long long)i);
-        if (rp[i] & 3) aligned = false;
-        if (len > max_len) max_len = len;
-        pstart[i] = pad_total;
-        pad_total += (len + 3) & ~(int64_t)3;
-    }
-    if (max_len > n) return set_error(ASYRK_EINVAL, "a row has more entries than n");
-    if (pad_total != rp[m]) aligned = false;
-    p->nnz = rp[m];
-    p->nnz_pad = aligned ? p->nnz : pad_total;
-    p->max_len = max_len;
-
-    // 2. device arrays
-    const size_t es = value_size(p->dtype);
-    int st;
-    if ((st = dev_alloc(p, &p->rec, (size_t)m)) != ASYRK_OK) return st;
-    if ((st = dev_alloc(p, &p->col, (size_t)p->nnz_pad)) != ASYRK_OK) return st;
-    if ((st = dev_alloc(p, (char **)&p->val, (size_t)p->nnz_pad * es)) != ASYRK_OK) return st;
-    if ((st = dev_alloc(p, &p->b64, (size_t)m)) != ASYRK_OK) return st;
-    if ((st = dev_alloc(p, &p->w64, (size_t)m)) != ASYRK_OK) return st;
-
-    // temporaries: the caller's layout on the device (when it is not already)
-    int64_t *rp_d = nullptr, *ps_d = nullptr;
+    // temporaries, freed on every exit path
+    int64_t *rp_d = nullptr, *ps_d = nullptr, *plen_d = nullptr, *scan_tmp = nullptr;
+    unsigned long long *info_d = nullptr;
     int32_t *col_src = nullptr;
     void *val_src = nullptr;
     double *b_d = nullptr;
     unsigned *err_d = nullptr;
-    uint2 *tab_d = nullptr;
+    bool own_src = false;
     auto cleanup = [&]() {
-        cudaFree(rp_d); cudaFree(ps_d); cudaFree(err_d); cudaFree(tab_d);
-        if (!on_dev) { cudaFree(b_d); if (!aligned) { cudaFree(col_src); cudaFree(val_src); } }
+        if (!on_dev) { cudaFree(rp_d); cudaFree(b_d); }
+        if (own_src) { cudaFree(col_src); cudaFree(val_src); }
+        cudaFree(ps_d); cudaFree(plen_d); cudaFree(scan_tmp); cudaFree(info_d); cudaFree(err_d);
     };
     auto fail = [&](int code) { cleanup(); return code; };
 #define ASYRK_CKC(call)                                                                    \
@@ -317,49 +267,82 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
         if (e__ != cudaSuccess) return fail(cuda_fail(e__, #call, __FILE__, __LINE__));    \
     } while (0)
 
-    ASYRK_CKC(cudaMalloc((void **)&rp_d, (m + 1) * sizeof(int64_t)));
-    ASYRK_CKC(cudaMemcpyAsync(rp_d, rp.data(), (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    // 1. row pointers on the device: checks, padded row starts (a prefix sum)
+    if (on_dev) {
+        rp_d = const_cast<int64_t *>(row_ptr);
+    } else {
+        ASYRK_CKC(cudaMalloc((void **)&rp_d, (m + 1) * sizeof(int64_t)));
+        ASYRK_CKC(cudaMemcpyAsync(rp_d, row_ptr, (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
+    ASYRK_CKC(cudaMalloc((void **)&plen_d, m * sizeof(int64_t)));
+    ASYRK_CKC(cudaMalloc((void **)&ps_d, (m + 1) * sizeof(int64_t)));
+    ASYRK_CKC(cudaMalloc((void **)&scan_tmp, scan_tmp_count(m) * sizeof(int64_t)));
+    ASYRK_CKC(cudaMalloc((void **)&info_d, 3 * sizeof(unsigned long long)));
+    ASYRK_CKC(cudaMemsetAsync(info_d, 0, 2 * sizeof(unsigned long long), s));
+    ASYRK_CKC(cudaMemsetAsync(info_d + 2, 0xff, sizeof(unsigned long long), s));
+    k_rowptr_pass<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, n, rp_d, plen_d, info_d);
+    ASYRK_CKC(cudaGetLastError());
+    int st = exclusive_scan(plen_d, ps_d, m, scan_tmp, ps_d + m, s);
+    if (st != ASYRK_OK) return fail(st);
+    unsigned long long info[3];
+    int64_t tail[2];  // rp[m], padded total
+    ASYRK_CKC(cudaMemcpyAsync(info, info_d, sizeof info, cudaMemcpyDeviceToHost, s));
+    ASYRK_CKC(cudaMemcpyAsync(&tail[0], rp_d + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ASYRK_CKC(cudaMemcpyAsync(&tail[1], ps_d + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ASYRK_CKC(cudaStreamSynchronize(s));
+    if (info[0] & RP_FIRST) return fail(set_error(ASYRK_EINVAL, "row_ptr[0] must be 0"));
+    if (info[0] & RP_EMPTY)
+        return fail(set_error(ASYRK_EINVAL, "row %llu is empty or row_ptr decreases (the problem "
+                              "has no zero rows)", info[2]));
+    if (info[0] & RP_LONG) return fail(set_error(ASYRK_EINVAL, "a row has more entries than n"));
+    const bool aligned = !(info[0] & RP_MISALIGNED) && tail[1] == tail[0];
+    p->nnz = tail[0];
+    p->nnz_pad = aligned ? p->nnz : tail[1];
+    p->max_len = (int64_t)info[1];
+
+    // 2. device arrays
+    const size_t es = value_size(p->dtype);
+    if ((st = dev_alloc(p, &p->rec, (size_t)m)) != ASYRK_OK) return fail(st);
+    if ((st = dev_alloc(p, &p->col, (size_t)p->nnz_pad)) != ASYRK_OK) return fail(st);
+    if ((st = dev_alloc(p, (char **)&p->val, (size_t)p->nnz_pad * es)) != ASYRK_OK) return fail(st);
+    if ((st = dev_alloc(p, &p->b64, (size_t)m)) != ASYRK_OK) return fail(st);
+    if ((st = dev_alloc(p, &p->w64, (size_t)m)) != ASYRK_OK) return fail(st);
     ASYRK_CKC(cudaMalloc((void **)&err_d, sizeof(unsigned)));
     ASYRK_CKC(cudaMemsetAsync(err_d, 0, sizeof(unsigned), s));
-    if (!aligned) {
-        ASYRK_CKC(cudaMalloc((void **)&ps_d, m * sizeof(int64_t)));
-        ASYRK_CKC(cudaMemcpyAsync(ps_d, pstart.data(), m * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    }
-    if (on_dev) {
+
+    // 3. the caller's entries: straight into place when rows are already
+    //    4-aligned, else through the row pass's padding copy
+    if (aligned) {
+        const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        ASYRK_CKC(cudaMemcpyAsync(p->col, col_idx, p->nnz * 4, kind, s));
+        ASYRK_CKC(cudaMemcpyAsync(p->val, values, p->nnz * es, kind, s));
+    } else if (on_dev) {
         col_src = const_cast<int32_t *>(col_idx);
         val_src = const_cast<void *>(values);
-        b_d = const_cast<double *>(b);
-        if (aligned) {
-            ASYRK_CKC(cudaMemcpyAsync(p->col, col_idx, p->nnz * 4, cudaMemcpyDeviceToDevice, s));
-            ASYRK_CKC(cudaMemcpyAsync(p->val, values, p->nnz * es, cudaMemcpyDeviceToDevice, s));
-        }
     } else {
-        if (aligned) {
-            col_src = p->col;
-            val_src = p->val;
-        } else {
-            ASYRK_CKC(cudaMalloc((void **)&col_src, p->nnz * 4));
-            ASYRK_CKC(cudaMalloc(&val_src, p->nnz * es));
-        }
+        own_src = true;
+        ASYRK_CKC(cudaMalloc((void **)&col_src, p->nnz * 4));
+        ASYRK_CKC(cudaMalloc(&val_src, p->nnz * es));
         ASYRK_CKC(cudaMemcpyAsync(col_src, col_idx, p->nnz * 4, cudaMemcpyHostToDevice, s));
         ASYRK_CKC(cudaMemcpyAsync(val_src, values, p->nnz * es, cudaMemcpyHostToDevice, s));
+    }
+    if (on_dev) {
+        b_d = const_cast<double *>(b);
+    } else {
         ASYRK_CKC(cudaMalloc((void **)&b_d, m * sizeof(double)));
         ASYRK_CKC(cudaMemcpyAsync(b_d, b, m * sizeof(double), cudaMemcpyHostToDevice, s));
     }
-    // with aligned input the row pass reads the final arrays in place
     const int32_t *rs_col = aligned ? p->col : col_src;
     const void *rs_val = aligned ? p->val : val_src;
+    const int64_t *pstart = aligned ? nullptr : ps_d;
     switch (p->dtype) {
-    case ASYRK_F64: launch_row_setup<double>(p, rp_d, ps_d, rs_col, rs_val, b_d, err_d, s); break;
-    case ASYRK_F32: launch_row_setup<float>(p, rp_d, ps_d, rs_col, rs_val, b_d, err_d, s); break;
-    default: launch_row_setup<bf16_t>(p, rp_d, ps_d, rs_col, rs_val, b_d, err_d, s); break;
+    case ASYRK_F64: launch_row_setup<double>(p, rp_d, pstart, rs_col, rs_val, b_d, err_d, s); break;
+    case ASYRK_F32: launch_row_setup<float>(p, rp_d, pstart, rs_col, rs_val, b_d, err_d, s); break;
+    default: launch_row_setup<bf16_t>(p, rp_d, pstart, rs_col, rs_val, b_d, err_d, s); break;
     }
     ASYRK_CKC(cudaGetLastError());
     unsigned err_h = 0;
     ASYRK_CKC(cudaMemcpyAsync(&err_h, err_d, sizeof err_h, cudaMemcpyDeviceToHost, s));
-    std::vector<double> w((size_t)m), bh((size_t)m);
-    ASYRK_CKC(cudaMemcpyAsync(w.data(), p->w64, m * sizeof(double), cudaMemcpyDeviceToHost, s));
-    ASYRK_CKC(cudaMemcpyAsync(bh.data(), p->b64, m * sizeof(double), cudaMemcpyDeviceToHost, s));
     ASYRK_CKC(cudaStreamSynchronize(s));
     if (err_h) {
         const char *why = (err_h & ERR_COL_RANGE)  ? "a column index is outside [0, n)"
@@ -370,22 +353,8 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
         return fail(set_error(ASYRK_EINVAL, "malformed problem: %s", why));
     }
 
-    // 3. alias table of the row weights
-    double F = 0.0, bb = 0.0;
-    for (int64_t i = 0; i < m; ++i) F += w[(size_t)i];
-    for (int64_t i = 0; i < m; ++i) bb += bh[(size_t)i] * bh[(size_t)i];
-    if (!(F > 0.0) || !isfinite(F)) return fail(set_error(ASYRK_EINVAL, "||A||_F^2 is not finite"));
-    p->frob2 = F;
-    p->bnorm = sqrt(bb);
-    std::vector<uint2> tab;
-    p->uniform = build_alias(w, F, tab) ? 1 : 0;
-    if (!p->uniform) {
-        ASYRK_CKC(cudaMalloc((void **)&tab_d, m * sizeof(uint2)));
-        ASYRK_CKC(cudaMemcpyAsync(tab_d, tab.data(), m * sizeof(uint2), cudaMemcpyHostToDevice, s));
-        k_set_alias<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, tab_d, p->rec);
-        ASYRK_CKC(cudaGetLastError());
-    }
-    ASYRK_CKC(cudaStreamSynchronize(s));
+    // 4. ||A||_F^2, ||b|| and the alias table of the row weights, on the GPU
+    if ((st = row_totals_and_alias(p, s)) != ASYRK_OK) return fail(st);
     cleanup();
 #undef ASYRK_CKC
     return ASYRK_OK;

@@ -60,7 +60,9 @@ def pin_alias_probabilities():
     keep = thr / 2.0**32
     p = keep.copy()
     np.add.at(p, alias.astype(np.int64), 1 - keep)
-    return np.max(np.abs(p / m - w / w.sum())) < 1e-6 / m
+    # every bucket that aliases to row i adds at most one 2^-32 quantum to p_i
+    n_alias = np.bincount(alias.astype(np.int64), minlength=m)
+    return bool(np.all(np.abs(p / m - w / w.sum()) <= (1 + n_alias) / 2.0**32 / m + 1e-15))
 
 
 def pin_philox_counter_words():
@@ -160,8 +162,12 @@ MUTATIONS = [
     ("alias coin inverted", "return (u[1] < thr[bucket]) ? (int64_t)bucket : (int64_t)alias[bucket];",
      "return (u[1] >= thr[bucket]) ? (int64_t)bucket : (int64_t)alias[bucket];",
      pin_row_frequencies),
-    ("Vose residual not carried", "q[l] = (q[l] + q[s]) - 1.0;", "q[l] = q[l] - 1.0;",
+    ("heavy's residual not carried to the next heavy", "R = M[heavy[t + 1]] - (U - R);",
+     "R = M[heavy[t + 1]];", pin_alias_probabilities),
+    ("light's deficit not taken from the heavy", "R -= U - M[l];", "R -= M[l];",
      pin_alias_probabilities),
+    ("rounding of the masses not redistributed",
+     "M[i] += D / m + (i < D % m ? 1 : 0);", "M[i] += 0;", pin_alias_probabilities),
     ("weights not squared", "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += val[k] * val[k];",
      "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += fabs(val[k]);",
      pin_row_frequencies),

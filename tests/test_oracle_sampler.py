@@ -2,7 +2,8 @@
 
 The paper fixes the row probabilities ||a_i||^2/||A||_F^2 (Section 1, before
 Eq. (2)); the generator behind them (Philox4x32-10, Salmon et al. SC'11) and the
-alias table (Vose) are this project's choice.  Each is pinned to something other
+alias table (Walker's method, built by one sweep over integer masses) are this
+project's choice.  Each is pinned to something other
 than the oracle itself:
   * Philox4x32-10 against cuRAND's host Philox4_32_10 generator, run here on the
     CPU (its documented layout: 65536 subsequences, counter word 2 = subsequence,
