@@ -729,6 +729,19 @@ def run_asyrk(args, dist):
                        "frac_of_probe_pairs": (32 * per_launch_proj / per_launch_s /
                                                probe["gather_red_pairs_per_s"])
                        if probe.get("gather_red_pairs_per_s") else None}}
+    # the workload's gamma sweep {0.5, 1}: time to tol and sweeps for each
+    gamma_sweep = None
+    if dist.rank == 0 and not args.no_extras:
+        gamma_sweep = []
+        for g in (0.5, 1.0):
+            x.zero_()
+            torch.cuda.synchronize()
+            st, info = p.solve(x, gamma=g, tol=args.tol, max_sweeps=max_sweeps, x_true=xt,
+                               device_ptrs=True, stream=stream, profile=True)
+            gamma_sweep.append({"gamma": g, "status": st, "ms": 1e3 * info.seconds,
+                                "sweeps": info.sweeps, "rel_err": info.rel_err,
+                                "applied_projections_per_s":
+                                    (info.projections - info.skipped) / info.seconds})
     p.close()
 
     # ---------------- end to end from host buffers ----------------
@@ -778,7 +791,8 @@ def run_asyrk(args, dist):
 
     extras = None
     if dist.rank == 0 and not args.no_extras:
-        extras = {"plain_and_refine": extras_plain_refine(asyrk, synth),
+        extras = {"gamma_sweep": gamma_sweep,
+                  "plain_and_refine": extras_plain_refine(asyrk, synth),
                   "table2": extras_table2(asyrk, synth, torch),
                   "least_squares": extras_lsq(asyrk, synth, torch),
                   "tau_study": extras_tau_study(asyrk, synth, torch),

@@ -1,5 +1,5 @@
 // scan.cu -- device-wide exclusive prefix sum of int64 (three passes: per-tile
-// scans with their totals, one thread over the tile totals, the add-back).
+// scans with their totals, one block over the tile totals, the add-back).
 // Integer sums are exact, so the result does not depend on the tiling.
 #include "common.cuh"
 #include "scan.cuh"
@@ -42,17 +42,34 @@ __global__ void k_scan_tiles(const int64_t *__restrict__ in, int64_t *__restrict
     }
 }
 
-__global__ void k_scan_sums(int64_t *__restrict__ tile_sum, int64_t tiles, int64_t *__restrict__ total)
+// one block of 1024 threads scans the tile totals in chunks of 1024, carrying
+// the running sum from chunk to chunk
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t *__restrict__ tile_sum, int64_t tiles,
+                                                    int64_t *__restrict__ total)
 {
-    // one thread: tile counts are small (count / 2048)
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t acc = 0;
-    for (int64_t k = 0; k < tiles; ++k) {
-        const int64_t x = tile_sum[k];
-        tile_sum[k] = acc;
-        acc += x;
+    __shared__ int64_t sh[1024];
+    __shared__ int64_t carry;
+    const int t = threadIdx.x;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < tiles; base += 1024) {
+        const int64_t i = base + t;
+        const int64_t v = i < tiles ? tile_sum[i] : 0;
+        sh[t] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan (Hillis-Steele)
+            const int64_t add = t >= o ? sh[t - o] : 0;
+            __syncthreads();
+            sh[t] += add;
+            __syncthreads();
+        }
+        const int64_t c = carry;
+        if (i < tiles) tile_sum[i] = c + sh[t] - v;
+        __syncthreads();
+        if (t == 1023) carry = c + sh[1023];
+        __syncthreads();
     }
-    *total = acc;
+    if (t == 0) *total = carry;
 }
 
 __global__ void k_scan_add(int64_t *__restrict__ out, const int64_t *__restrict__ tile_sum,
@@ -73,7 +90,7 @@ int exclusive_scan(const int64_t *in, int64_t *out, int64_t count, int64_t *tmp,
         return ASYRK_OK;
     }
     k_scan_tiles<<<(unsigned)tiles, 256, 0, s>>>(in, out, tmp, count);
-    k_scan_sums<<<1, 32, 0, s>>>(tmp, tiles, total);
+    k_scan_sums<<<1, 1024, 0, s>>>(tmp, tiles, total);
     k_scan_add<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(out, tmp, count);
     ASYRK_CK(cudaGetLastError());
     return ASYRK_OK;
