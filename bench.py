@@ -359,7 +359,8 @@ TABLE2 = [(80000, 100000, 0.0005, 3.6, 195), (80000, 100000, 0.001, 7.6, 284),
 def extras_table2(asyrk, synth, torch):
     """Table 2's shapes: Section 5's generator (delta*m*n random positions, so
     Poisson(delta*n) row lengths; unit rows), FP32 async, stop on
-    ||A^T(Ax - b)||^2 <= 1e-5 checked every sweep; with i.i.d. weighted draws
+    ||A^T(Ax - b)||^2 <= 1e-5 checked at adaptive intervals (half the sweeps the
+    measured contraction still needs); with i.i.d. weighted draws
     and with Section 5's shuffled sweeps (rows without replacement)."""
     rows = []
     for k, (m, n, delta, t_paper, ep_paper) in enumerate(TABLE2):
@@ -379,7 +380,8 @@ def extras_table2(asyrk, synth, torch):
                 p.position = 0
                 torch.cuda.synchronize()
                 st, info = p.solve(x, tol=1e-5, max_sweeps=3000, device_ptrs=True, profile=True,
-                                   measure=asyrk.MEASURE_NORMAL_RESIDUAL, sampling=sampling)
+                                   measure=asyrk.MEASURE_NORMAL_RESIDUAL, sampling=sampling,
+                                   check_every=0)
                 if best is None or info.seconds < best[1].seconds:
                     best = (st, info)
             st, info = best
@@ -394,7 +396,8 @@ def extras_table2(asyrk, synth, torch):
                          "speedup_vs_paper_time": t_paper / info.seconds})
         p.close()
     return {"workload": "Table 2 shapes; Section 5's generator with unit rows, FP32 values and "
-                        "iterate; stop ||A^T(Ax-b)||^2 <= 1e-5 (absolute), checked every sweep; "
+                        "iterate; stop ||A^T(Ax-b)||^2 <= 1e-5 (absolute), checked at adaptive "
+                        "intervals (check_every=0); "
                         "the paper's numbers are 10 cores of an unnamed Intel Xeon (context)",
             "rows": rows}
 
@@ -420,7 +423,8 @@ def extras_tau_study(asyrk, synth, torch):
             p.position = 0
             torch.cuda.synchronize()
             st, info = p.solve(x, tol=1e-4, max_sweeps=3000, workers=W, device_ptrs=True,
-                               measure=asyrk.MEASURE_RESIDUAL, sampling=asyrk.SAMPLE_SHUFFLED)
+                               measure=asyrk.MEASURE_RESIDUAL, sampling=asyrk.SAMPLE_SHUFFLED,
+                               check_every=0)
             rows.append({"workers": info.workers, "status": st, "ms": 1e3 * info.seconds,
                          "epochs_n_iterations": info.projections / n,
                          "skipped_fraction": info.skipped / max(1, info.projections + info.skipped),

@@ -140,7 +140,10 @@ typedef struct asyrk_solve_opts {
     int32_t device_ptrs;     /* 1: x and x_true are device pointers (double)         */
     int32_t workers;         /* concurrent row workers; 0 = automatic (ASYNC/REFINE)  */
     int32_t subwarp;         /* lanes per row: 0 = automatic, or 1, 2, 4, 8, 16, 32   */
-    int64_t check_every;     /* sweeps between convergence checks; >= 1              */
+    int64_t check_every;     /* sweeps between convergence checks (>= 1); 0: adaptive,
+                                half the sweeps the measured contraction still needs,
+                                from 1 up to twice the last interval (SEQUENTIAL and
+                                ASYNC; REFINE checks every outer step)              */
     const double *x_true;    /* optional x*; checks then use ||x-x*||/||x*||          */
     void *stream;            /* cudaStream_t; NULL = legacy default stream           */
     double inner_tol;        /* REFINE: inner solve's target relative decrease (0: 1e-3) */
@@ -214,7 +217,7 @@ void asyrk_destroy(asyrk_problem *p);
  * position (asyrk_set_position) and the position advances by the
  * projections done.
  * Returns OK, NOT_CONVERGED, DIVERGED, or EINVAL (gamma outside (0, 2),
- * check_every < 1, max_sweeps < 0, mode or subwarp unknown, workers < 0),
+ * check_every < 0, max_sweeps < 0, mode or subwarp unknown, workers < 0),
  * ENOMEM, ECUDA.  info may be NULL. */
 int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol, int64_t max_sweeps,
                 const asyrk_solve_opts *opts, asyrk_solve_info *info);

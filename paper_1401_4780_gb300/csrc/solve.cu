@@ -96,6 +96,25 @@ static bool diverged(double meas, double meas0)
     return !isfinite(meas) || meas > 1e30 * (meas0 > 0.0 ? meas0 : 1.0);
 }
 
+// Adaptive check interval (check_every = 0): from the contraction the last k
+// sweeps achieved, rho = (meas / prev)^(1/k) per sweep, the sweeps still needed
+// are log(tol / meas) / log(rho); the next check comes after half of them (at
+// least 1, at most twice the last interval), so the interval shrinks to one
+// sweep as the tolerance nears and at most a sweep is run past it.  Without a
+// measured contraction the interval stays at one sweep.
+static int64_t next_check(double prev, double meas, int64_t k, double tol)
+{
+    if (!(tol > 0.0)) return 2 * k;  // fixed sweep count: checks only watch for divergence
+    if (!(meas > 0.0) || !(prev > meas) || !(meas > tol)) return 1;
+    const double rho = pow(meas / prev, 1.0 / (double)k);
+    if (!(rho > 0.0 && rho < 1.0)) return 1;
+    const double need = log(tol / meas) / log(rho);
+    double next = ceil(0.5 * need);
+    if (next < 1.0) next = 1.0;
+    if (next > 2.0 * (double)k) next = 2.0 * (double)k;
+    return (int64_t)next;
+}
+
 static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps,
                        const asyrk_solve_opts &o, asyrk_solve_info &info)
 {
@@ -137,8 +156,11 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
     int status = (tol > 0.0 && meas <= tol) ? ASYRK_OK : ASYRK_NOT_CONVERGED;
     int64_t sweeps = 0;
     const unsigned long long m = (unsigned long long)p->m;
+    const bool adaptive = o.check_every == 0;
+    int64_t k_next = 1;
+    double meas_prev = meas0;
     while (status == ASYRK_NOT_CONVERGED && sweeps < max_sweeps) {
-        int64_t k = o.check_every;
+        int64_t k = adaptive ? k_next : o.check_every;
         if (k > max_sweeps - sweeps) k = max_sweeps - sweeps;
         ProjectLaunch L;
         L.p = p;
@@ -166,6 +188,8 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
             break;
         }
         if (tol > 0.0 && meas <= tol) status = ASYRK_OK;
+        if (adaptive) k_next = next_check(meas_prev, meas, k, tol);
+        meas_prev = meas;
     }
     if (tol <= 0.0 && status == ASYRK_NOT_CONVERGED && sweeps == max_sweeps) status = ASYRK_OK;
     info.sweeps = sweeps;
@@ -285,7 +309,7 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
     if (opts) o = *opts;
     if (o.mode < ASYRK_MODE_SEQUENTIAL || o.mode > ASYRK_MODE_REFINE)
         return set_error(ASYRK_EINVAL, "unknown mode %d", o.mode);
-    if (o.check_every < 1) return set_error(ASYRK_EINVAL, "check_every must be >= 1");
+    if (o.check_every < 0) return set_error(ASYRK_EINVAL, "check_every must be >= 0");
     if (o.workers < 0) return set_error(ASYRK_EINVAL, "workers < 0");
     if (o.subwarp != 0 && o.subwarp != 1 && o.subwarp != 2 && o.subwarp != 4 && o.subwarp != 8 &&
         o.subwarp != 16 && o.subwarp != 32)

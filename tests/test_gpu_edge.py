@@ -70,7 +70,7 @@ def test_well_formed_base_is_accepted():
 
 
 @pytest.mark.parametrize("bad", [{"gamma": 0.0}, {"gamma": 2.0}, {"max_sweeps": -1},
-                                 {"check_every": 0}, {"subwarp": 3}, {"workers": -2},
+                                 {"check_every": -1}, {"subwarp": 3}, {"workers": -2},
                                  {"mode": 9}])
 def test_solve_argument_errors(bad):
     s = synth.make_system(64, 16, 4, 1)

@@ -161,3 +161,33 @@ def test_device_pointer_create_and_solve():
         assert st == asyrk.OK
         stream.synchronize()
         assert _rel(x.cpu().numpy(), _oracle_steps(s, seed, 2 * s.m)) <= 1e-12
+
+
+@pytest.mark.parametrize("kind", ["spiky", "one_heavy", "near_unit", "tiny_m1", "tiny_m2",
+                                  "tiny_m3", "two_levels"])
+def test_alias_table_built_on_the_gpu_matches_the_oracle(kind):
+    rng = np.random.default_rng(11)
+    if kind == "spiky":
+        w = np.array([1e-12, 1.0, 1e6, 3.0, 1e-3, 7.0, 2.0] * 300)
+    elif kind == "one_heavy":
+        w = np.ones(5000)
+        w[1234] = 1e7
+    elif kind == "near_unit":
+        w = 1.0 + rng.integers(-3, 4, size=4096) * np.finfo(np.float64).eps
+    elif kind.startswith("tiny_m"):
+        w = np.exp(rng.standard_normal(int(kind[-1])))
+    else:
+        w = np.where(rng.random(70000) < 0.5, 1.0, 2.0)
+    m = w.size
+    val = np.sqrt(w)
+    row_ptr = np.arange(m + 1, dtype=np.int64)
+    col = np.arange(m, dtype=np.int32)
+    b = val * rng.standard_normal(m)
+    samp = oracle.Sampler(m, row_ptr, val)
+    with asyrk.Problem(m, m, row_ptr, col, val, asyrk.F64, b, seed=77) as p:
+        assert p.stats()["uniform"] == samp.uniform
+        assert p.stats()["frob2"] == samp.F  # the same blocked FP64 sum
+        for j0, count in [(0, 300_000), (2**33 + 5, 10_000)]:
+            np.testing.assert_array_equal(
+                p.draw_rows(j0, count, 3),
+                oracle.draw_rows(77, 3, j0, count, samp.thr, samp.alias, samp.uniform))

@@ -117,6 +117,38 @@ def test_alias_uniform_shortcut_only_for_identical_weights():
     assert uniform == 0
 
 
+def _masses(thr, alias, m):
+    """Units of 2^-32 of a bucket that the table gives each row."""
+    M = thr.astype(np.int64).copy()
+    full = thr == 0xFFFFFFFF
+    M[full] = 1 << 32  # a full bucket (2^32 - 1 is the stored maximum)
+    np.add.at(M, alias.astype(np.int64), np.where(full, 0, (1 << 32) - M))
+    return M
+
+
+@pytest.mark.parametrize("scale", [1.0, 1.0 - 1e-9])
+def test_alias_masses_add_up_exactly_and_overshoot_comes_off_the_largest(scale):
+    # scale < 1 shrinks F, so the floors of q_i 2^32 overshoot m 2^32 (D < 0):
+    # the overshoot must come off the first row of largest mass, nothing else moves
+    m = 1000
+    w = np.exp(2 * np.random.default_rng(8).standard_normal(m))
+    F = float(np.sum(w)) * scale
+    thr, alias, uniform = oracle.alias_table(w, F)
+    M = _masses(thr, alias, m)
+    assert int(M.sum()) == m << 32
+    base = np.floor(((w * float(m)) / F) * 4294967296.0).astype(np.int64)
+    D = (m << 32) - int(base.sum())
+    if scale < 1.0:
+        assert D < 0
+        a = int(np.argmax(base))
+        want = base.copy()
+        want[a] += D
+    else:
+        assert 0 <= D < m
+        want = base + (np.arange(m) < D)
+    np.testing.assert_array_equal(M, want)
+
+
 def test_drawn_rows_follow_row_weights_chi_square():
     m = 64
     rng = np.random.default_rng(5)
