@@ -44,7 +44,24 @@ struct SolveCtx {
 static int project(SolveCtx &c, const ProjectLaunch &L)
 {
     if (c.profile) ASYRK_CK(cudaEventRecord(c.p->ev[0], c.s));
-    int st = launch_project(L);
+    int st = ASYRK_OK;
+    const unsigned long long m = (unsigned long long)c.p->m;
+    if (L.sampling == ASYRK_SAMPLE_SHUFFLED && L.count > m - L.j0 % m) {
+        // shuffled sweeps run one launch per sweep: within a sweep every row
+        // comes once, so no worker finds its row held by a worker of the next
+        // sweep (a skip would drop that row's visit for the sweep)
+        ProjectLaunch one = L;
+        unsigned long long done = 0;
+        while (done < L.count && st == ASYRK_OK) {
+            one.j0 = L.j0 + done;
+            const unsigned long long to_boundary = m - one.j0 % m;
+            one.count = L.count - done < to_boundary ? L.count - done : to_boundary;
+            st = launch_project(one);
+            done += one.count;
+        }
+    } else {
+        st = launch_project(L);
+    }
     if (st != ASYRK_OK) return st;
     if (c.profile) {
         ASYRK_CK(cudaEventRecord(c.p->ev[1], c.s));

@@ -97,7 +97,8 @@ def test_first_table2_shape_full_size():
     assert float(g @ g) <= 1e-5
 
 
-def test_adaptive_check_interval_stops_at_the_same_place_with_few_checks():
+@pytest.mark.parametrize("sampling", [asyrk.SAMPLE_WEIGHTED, asyrk.SAMPLE_SHUFFLED])
+def test_adaptive_check_interval_stops_at_the_same_place_with_few_checks(sampling):
     s = synth.make_system(8000, 10000, ("poisson", 10), 41, row_norms="unit", value_dtype="f32")
     runs = {}
     with asyrk.Problem.from_system(s) as p:
@@ -105,11 +106,14 @@ def test_adaptive_check_interval_stops_at_the_same_place_with_few_checks():
             p.position = 0
             x = np.zeros(s.n)
             st, info = p.solve(x, tol=1e-5, max_sweeps=3000, check_every=every,
-                               measure=asyrk.MEASURE_NORMAL_RESIDUAL)
+                               measure=asyrk.MEASURE_NORMAL_RESIDUAL, sampling=sampling)
             assert st == asyrk.OK, info.as_dict()
             assert _normal2(s, x) <= 1e-5
             runs[every] = info
     fixed, adaptive = runs[1], runs[0]
+    if sampling == asyrk.SAMPLE_SHUFFLED:
+        # a multi-sweep interval still runs sweep by sweep: no row is held twice
+        assert adaptive.skipped == 0 and fixed.skipped == 0
     # the same row sequence, stopped at most a couple of sweeps later ...
     assert fixed.sweeps <= adaptive.sweeps <= 1.1 * fixed.sweeps + 2
     # ... after far fewer measurements (each check is one launch or more)
