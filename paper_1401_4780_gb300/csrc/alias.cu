@@ -29,16 +29,23 @@ constexpr long long UNIT = 1LL << 32;
 
 inline unsigned blocks_for(int64_t count) { return (unsigned)((count + 255) / 256); }
 
-__global__ void k_block_sums(const double *__restrict__ v, int64_t m, int square,
-                             double *__restrict__ part)
+// one CTA per block of F_BLOCK rows: the block's values are staged in shared
+// memory by coalesced loads, then one thread adds them in index order
+__global__ void __launch_bounds__(256) k_block_sums(const double *__restrict__ v, int64_t m,
+                                                    int square, double *__restrict__ part)
 {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t lo = b * F_BLOCK;
-    if (lo >= m) return;
-    const int64_t hi = lo + F_BLOCK < m ? lo + F_BLOCK : m;
+    __shared__ double sh[F_BLOCK];
+    const int64_t lo = (int64_t)blockIdx.x * F_BLOCK;
+    const int len = (int)(m - lo < F_BLOCK ? m - lo : F_BLOCK);
+    for (int i = threadIdx.x; i < len; i += 256) {
+        const double x = v[lo + i];
+        sh[i] = square ? __dmul_rn(x, x) : x;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double s = 0.0;
-    for (int64_t i = lo; i < hi; ++i) s = __dadd_rn(s, square ? __dmul_rn(v[i], v[i]) : v[i]);
-    part[b] = s;
+    for (int i = 0; i < len; ++i) s = __dadd_rn(s, sh[i]);
+    part[blockIdx.x] = s;
 }
 
 __global__ void k_seq_sum(const double *__restrict__ part, int64_t nb, double *__restrict__ out)
@@ -243,9 +250,9 @@ int row_totals_and_alias(asyrk_problem *p, cudaStream_t s)
     if ((st = t.alloc(&part, (size_t)nb)) || (st = t.alloc(&sums, 2)) ||
         (st = t.alloc(&differs, 1)) || (st = t.alloc(&acc, 3)))
         return st;
-    k_block_sums<<<blocks_for(nb), 256, 0, s>>>(p->w64, m, 0, part);
+    k_block_sums<<<(unsigned)nb, 256, 0, s>>>(p->w64, m, 0, part);
     k_seq_sum<<<1, 32, 0, s>>>(part, nb, sums);
-    k_block_sums<<<blocks_for(nb), 256, 0, s>>>(p->b64, m, 1, part);
+    k_block_sums<<<(unsigned)nb, 256, 0, s>>>(p->b64, m, 1, part);
     k_seq_sum<<<1, 32, 0, s>>>(part, nb, sums + 1);
     ASYRK_CK(cudaMemsetAsync(differs, 0, sizeof(unsigned), s));
     k_differs<<<blocks_for(m), 256, 0, s>>>(p->w64, m, differs);
