@@ -317,30 +317,6 @@ __device__ __forceinline__ double slot_value(int dtype, const void *val, long lo
     return (double)static_cast<const float *>(val)[k];
 }
 
-// a_i^T x for the rows [lo, hi) of a slot, 8 lanes per row (entries strided
-// by 8, a shuffle reduction); f(i, a_i^T x) runs on each row's first lane.
-// Every thread of the block makes the same number of passes (the shuffles).
-template <typename XF, typename F>
-__device__ __forceinline__ void rows_dot8(const SysDesc &D, long long lo, long long hi, XF xval,
-                                          F f)
-{
-    const int g = threadIdx.x >> 3, sl = threadIdx.x & 7;
-    const long long passes = (hi - lo + 31) / 32;
-    for (long long it = 0; it < passes; ++it) {
-        const long long i = lo + g + 32 * it;
-        double acc = 0.0;
-        if (i < hi) {
-            const RowRec r = D.rec[i];
-            for (unsigned q = sl; q < r.len; q += 8)
-                acc += slot_value(D.dtype, D.val, r.start + q) * xval(D.col[r.start + q]);
-        }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        if (i < hi && sl == 0) f(i, acc);
-    }
-}
-
 // measure_only: the first measure before any sweep (also ||x*|| when ref < 0)
 __global__ void __launch_bounds__(256) k_batch_check(SysDesc *d, int count, double *part,
                                                      int measure_only)
@@ -366,13 +342,17 @@ __global__ void __launch_bounds__(256) k_batch_check(SysDesc *d, int count, doub
         const long long lo = (long long)k * BATCH_ROW_CHUNK;
         long long hi = lo + BATCH_ROW_CHUNK;
         if (hi > D.m) hi = D.m;
-        rows_dot8(D, lo, hi, [&](int t) { return (double)__ldcg(D.x + t); },
-                  [&](long long i, double acc) {
-                      const double bi = D.bvec ? (double)D.bvec[i] : (double)D.rec[i].b;
-                      const double ri = bi - acc;
-                      v0 += ri * ri;
-                      v1 += bi * bi;
-                  });
+        for (long long i = lo + threadIdx.x; i < hi; i += 256) {
+            const RowRec r = D.rec[i];
+            double acc = 0.0;
+            for (unsigned q = 0; q < r.len; ++q)
+                acc += slot_value(D.dtype, D.val, r.start + q) *
+                       (double)__ldcg(D.x + D.col[r.start + q]);
+            const double bi = D.bvec ? (double)D.bvec[i] : (double)r.b;
+            const double ri = bi - acc;
+            v0 += ri * ri;
+            v1 += bi * bi;
+        }
     }
     double t0, t1;
     if (!slot_reduce(v0, v1, part, c, D.chunk0, D.nchunks, &D.chk_count, t0, t1)) return;
@@ -430,11 +410,15 @@ __global__ void __launch_bounds__(256) k_batch_residual(SysDesc *d, int count, d
     const long long lo = (long long)k * BATCH_ROW_CHUNK;
     long long hi = lo + BATCH_ROW_CHUNK;
     if (hi > D.m) hi = D.m;
-    rows_dot8(D, lo, hi, [&](int t) { return D.x64[t]; }, [&](long long i, double acc) {
+    for (long long i = lo + threadIdx.x; i < hi; i += 256) {
+        const RowRec r = D.rec[i];
+        double acc = 0.0;
+        for (unsigned q = 0; q < r.len; ++q)
+            acc += slot_value(D.dtype, D.val, r.start + q) * D.x64[D.col[r.start + q]];
         const double ri = D.b64[i] - acc;
         v0 += ri * ri;
         v1 += D.b64[i] * D.b64[i];
-    });
+    }
     double t0, t1;
     if (!slot_reduce(v0, v1, part, c, D.chunk0, D.nchunks, &D.res_count, t0, t1)) return;
     D.res2 = t0;
@@ -472,11 +456,15 @@ __global__ void __launch_bounds__(256) k_batch_outer_residual(SysDesc *d, int co
         const long long lo = (long long)k * BATCH_ROW_CHUNK;
         long long hi = lo + BATCH_ROW_CHUNK;
         if (hi > D.m) hi = D.m;
-        rows_dot8(D, lo, hi, [&](int t) { return D.x64[t]; }, [&](long long i, double acc) {
+        for (long long i = lo + threadIdx.x; i < hi; i += 256) {
+            const RowRec r = D.rec[i];
+            double acc = 0.0;
+            for (unsigned q = 0; q < r.len; ++q)
+                acc += slot_value(D.dtype, D.val, r.start + q) * D.x64[D.col[r.start + q]];
             const double ri = D.b64[i] - acc;
             D.r32[i] = (float)ri;
             v0 += ri * ri;
-        });
+        }
     }
     if (D.xt) {
         const long long lo = (long long)k * BATCH_ERR_CHUNK;

@@ -106,7 +106,8 @@ def test_adaptive_check_interval_stops_at_the_same_place_with_few_checks(samplin
             p.position = 0
             x = np.zeros(s.n)
             st, info = p.solve(x, tol=1e-5, max_sweeps=3000, check_every=every,
-                               measure=asyrk.MEASURE_NORMAL_RESIDUAL, sampling=sampling)
+                               measure=asyrk.MEASURE_NORMAL_RESIDUAL, sampling=sampling,
+                               profile=True)
             assert st == asyrk.OK, info.as_dict()
             assert _normal2(s, x) <= 1e-5
             runs[every] = info
@@ -114,7 +115,9 @@ def test_adaptive_check_interval_stops_at_the_same_place_with_few_checks(samplin
     if sampling == asyrk.SAMPLE_SHUFFLED:
         # a multi-sweep interval still runs sweep by sweep: no row is held twice
         assert adaptive.skipped == 0 and fixed.skipped == 0
-    # the same row sequence, stopped at most a couple of sweeps later ...
-    assert fixed.sweeps <= adaptive.sweeps <= 1.1 * fixed.sweeps + 2
-    # ... after far fewer measurements (each check is one launch or more)
-    assert adaptive.kernel_launches < 0.25 * fixed.kernel_launches
+    # the same row sequence, stopped within a few sweeps of the every-sweep check (the
+    # two runs interleave their workers differently, so either may need a sweep more) ...
+    assert abs(adaptive.sweeps - fixed.sweeps) <= 0.05 * fixed.sweeps + 2
+    # ... after far fewer checks (one per check interval)
+    assert fixed.project_launches == fixed.sweeps
+    assert adaptive.project_launches < 0.25 * fixed.project_launches
