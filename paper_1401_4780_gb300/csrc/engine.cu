@@ -213,34 +213,39 @@ __device__ __forceinline__ unsigned long long batch_run_g(const ProjArgs &a, int
 }
 
 template <bool EXCL>
-__global__ void __launch_bounds__(256, 3) k_batch_project(SysDesc *d, int count)  // <= 85 registers
+__global__ void __launch_bounds__(256, 4) k_batch_project(SysDesc *d, int count)  // <= 64 registers
 {
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int s = find_slot_warp(d, count, gw);
     if (s < 0) return;
     const SysDesc &D = d[s];
     if (!D.active || D.phase != 0 || gw >= D.warp0 + D.nwarps) return;  // warp-uniform
-    ProjArgs a;
-    a.rec = D.rec;
-    a.col = D.col;
-    a.val = D.val;
-    a.x = D.x;
-    a.b64 = nullptr;
-    a.w64 = nullptr;
-    a.key = D.key;
-    a.m = D.m;
-    a.uniform = D.uniform;
-    a.stream_id = D.stream_id;
-    a.j0 = D.j;
-    a.count = (unsigned long long)D.m * (unsigned long long)(D.k > 1 ? D.k : 1);  // k sweeps
-    a.workers = (long long)D.nwarps * (32 / D.G);
-    a.gamma = (double)D.gamma;
-    a.bvec = D.bvec;
-    a.sampling = D.sampling;
-    a.shuf_h = D.shuf_h;
-    a.update = D.update;
-    a.busy = D.busy;
-    a.skipped = nullptr;
+    // the warp's launch arguments live in shared memory, not registers
+    __shared__ ProjArgs sa[8];
+    ProjArgs &a = sa[threadIdx.x >> 5];
+    if ((threadIdx.x & 31) == 0) {
+        a.rec = D.rec;
+        a.col = D.col;
+        a.val = D.val;
+        a.x = D.x;
+        a.b64 = nullptr;
+        a.w64 = nullptr;
+        a.key = D.key;
+        a.m = D.m;
+        a.uniform = D.uniform;
+        a.stream_id = D.stream_id;
+        a.j0 = D.j;
+        a.count = (unsigned long long)D.m * (unsigned long long)(D.k > 1 ? D.k : 1);  // k sweeps
+        a.workers = (long long)D.nwarps * (32 / D.G);
+        a.gamma = (double)D.gamma;
+        a.bvec = D.bvec;
+        a.sampling = D.sampling;
+        a.shuf_h = D.shuf_h;
+        a.update = D.update;
+        a.busy = D.busy;
+        a.skipped = nullptr;
+    }
+    __syncwarp();
     const int rel = gw - D.warp0;
     const unsigned long long sk = (D.dtype == ASYRK_BF16)
                                       ? batch_run_g<bf16_t, EXCL>(a, D.G, rel)
