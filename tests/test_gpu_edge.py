@@ -151,3 +151,38 @@ def test_single_entry_rows_and_many_workers():
         st, info = p.solve(x, tol=1e-12, max_sweeps=200, x_true=xs, workers=512)
         assert st == asyrk.OK and info.workers == 512
         assert np.max(np.abs(x - xs)) <= 1e-12 * np.max(np.abs(xs))
+
+
+def test_half_a_billion_rows_64bit_offsets():
+    """m = 2^29 + 7 rows of one entry each (padded to 4: 2^31 + 28 stored
+    entries, so row starts pass 2^31): the alias table built on the GPU over the
+    whole m draws the three weight classes in proportion (chi-square), and one
+    sweep solves the diagonal-block system (each column's rows agree)."""
+    import torch
+    from scipy import stats
+    m, n = (1 << 29) + 7, 1 << 20
+    dev = "cuda"
+    i = torch.arange(m, dtype=torch.int64, device=dev)
+    row_ptr = torch.arange(m + 1, dtype=torch.int64, device=dev)
+    col = (i % n).to(torch.int32)
+    val = (1 + (i % 3)).to(torch.float32)
+    x_true = torch.linspace(-1.0, 1.0, n, dtype=torch.float64, device=dev)
+    b = val.double() * x_true[col.long()]
+    del i
+    torch.cuda.synchronize()
+    with asyrk.Problem(m, n, row_ptr, col, val, asyrk.F32, b, seed=5, device_ptrs=True) as p:
+        del row_ptr, col, b
+        st_ = p.stats()
+        assert st_["m"] == m and st_["nnz_padded"] == 4 * m and st_["uniform"] == 0
+        rows = p.draw_rows(2**33 + 11, 1 << 20)
+        assert rows.min() >= 0 and rows.max() < m
+        counts = np.bincount(rows % 3, minlength=3)
+        sizes = np.array([(m + 2) // 3, (m + 1) // 3, m // 3], dtype=np.float64)
+        expected = sizes * np.array([1.0, 4.0, 9.0])
+        expected = expected / expected.sum() * rows.size
+        assert stats.chisquare(counts, expected).pvalue > 1e-4
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        st, info = p.solve(x, tol=1e-6, max_sweeps=3, device_ptrs=True, x_true=x_true)
+        assert st == asyrk.OK, info.as_dict()
+    del val
+    torch.cuda.empty_cache()
