@@ -142,8 +142,9 @@ typedef struct asyrk_solve_opts {
     int32_t subwarp;         /* lanes per row: 0 = automatic, or 1, 2, 4, 8, 16, 32   */
     int64_t check_every;     /* sweeps between convergence checks (>= 1); 0: adaptive,
                                 half the sweeps the measured contraction still needs,
-                                from 1 up to twice the last interval (SEQUENTIAL and
-                                ASYNC; REFINE checks every outer step)              */
+                                from 1 up to twice the last interval and a tenth of
+                                the sweeps done (SEQUENTIAL and ASYNC; REFINE checks
+                                every outer step)                                    */
     const double *x_true;    /* optional x*; checks then use ||x-x*||/||x*||          */
     void *stream;            /* cudaStream_t; NULL = legacy default stream           */
     double inner_tol;        /* REFINE: inner solve's target relative decrease (0: 1e-3) */

@@ -115,20 +115,24 @@ static bool diverged(double meas, double meas0)
 
 // Adaptive check interval (check_every = 0): from the contraction the last k
 // sweeps achieved, rho = (meas / prev)^(1/k) per sweep, the sweeps still needed
-// are log(tol / meas) / log(rho); the next check comes after half of them (at
-// least 1, at most twice the last interval), so the interval shrinks to one
-// sweep as the tolerance nears and at most a sweep is run past it.  Without a
-// measured contraction the interval stays at one sweep.
-static int64_t next_check(double prev, double meas, int64_t k, double tol)
+// are log(tol / meas) / log(rho); the next check comes after half of them, at
+// least 1 sweep, at most twice the last interval and at most a tenth of the
+// sweeps done so far -- so a solve stops at most 10 % past the sweep where the
+// tolerance was met, and checks O(log sweeps) times when the decay is steady.
+// Without a measured contraction the interval is one sweep.
+static int64_t next_check(double prev, double meas, int64_t k, int64_t done, double tol)
 {
-    if (!(tol > 0.0)) return 2 * k;  // fixed sweep count: checks only watch for divergence
+    int64_t cap = done / 10;
+    if (cap < 1) cap = 1;
+    if (cap > 2 * k) cap = 2 * k;
+    if (!(tol > 0.0)) return cap;  // fixed sweep count: checks only watch for divergence
     if (!(meas > 0.0) || !(prev > meas) || !(meas > tol)) return 1;
     const double rho = pow(meas / prev, 1.0 / (double)k);
     if (!(rho > 0.0 && rho < 1.0)) return 1;
     const double need = log(tol / meas) / log(rho);
     double next = ceil(0.5 * need);
     if (next < 1.0) next = 1.0;
-    if (next > 2.0 * (double)k) next = 2.0 * (double)k;
+    if (next > (double)cap) next = (double)cap;
     return (int64_t)next;
 }
 
@@ -205,7 +209,7 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
             break;
         }
         if (tol > 0.0 && meas <= tol) status = ASYRK_OK;
-        if (adaptive) k_next = next_check(meas_prev, meas, k, tol);
+        if (adaptive) k_next = next_check(meas_prev, meas, k, sweeps, tol);
         meas_prev = meas;
     }
     if (tol <= 0.0 && status == ASYRK_NOT_CONVERGED && sweeps == max_sweeps) status = ASYRK_OK;
