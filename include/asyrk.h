@@ -183,7 +183,7 @@ typedef struct asyrk_problem_stats {
     int64_t nnz_padded;       /* stored entries after padding rows to 4-aligned starts */
     int64_t max_row_len;      /* mu = max_i ||a_i||_0 (Section 1 notation)           */
     int64_t device_bytes;     /* device memory held by the handle                    */
-    double frob2;             /* ||A||_F^2 in FP64                                   */
+    double frob2;             /* ||A||_F^2 in FP64, summed as the alias table states */
     int32_t dtype;            /* asyrk_dtype of the stored values                   */
     int32_t uniform;          /* 1: all row weights bit-identical, no alias table    */
     uint64_t seed;            /* Philox key                                          */

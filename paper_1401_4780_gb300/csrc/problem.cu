@@ -17,7 +17,8 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <vector>
+#include <new>
+
 
 #include "alias.cuh"
 #include "common.cuh"
