@@ -169,6 +169,7 @@ struct ProjectLaunch {
     int sampling = 0;               // 0: weighted i.i.d. draws, 1: shuffled sweeps
     int update = 0;                 // 0: the whole row, 1: one coordinate (Algorithm 1)
     bool b_from_rec = true;         // FP32 b from rec (else b64)
+    const unsigned long long *dyn = nullptr;  // device {j0, count} (graph-captured loop)
     cudaStream_t stream = nullptr;
 };
 int launch_project(const ProjectLaunch &L);  // counts into L.p->launches

@@ -196,7 +196,8 @@ __device__ __forceinline__ int find_slot_chunk(const SysDesc *d, int count, int 
 template <typename VT, int G, bool EXCL>
 __device__ __forceinline__ unsigned long long batch_run(const ProjArgs &a, int rel_warp)
 {
-    return run_workers<VT, float, G, false, EXCL>(a, (long long)rel_warp * (32 / G), a.workers);
+    return run_workers<VT, float, G, false, EXCL, false>(a, (long long)rel_warp * (32 / G),
+                                                         a.workers);
 }
 
 template <typename VT, bool EXCL>
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(256, 4) k_batch_project(SysDesc *d, int count)
         a.update = D.update;
         a.busy = D.busy;
         a.skipped = nullptr;
+        a.dyn = nullptr;
     }
     __syncwarp();
     const int rel = gw - D.warp0;

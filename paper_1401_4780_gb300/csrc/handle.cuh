@@ -45,4 +45,6 @@ struct asyrk_problem {
     int32_t *rows_buf = nullptr;
     int64_t rows_cap = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    void *loop_state = nullptr;        // device state of the graph-captured solve loop
+    cudaStream_t cap_stream = nullptr; // stream the loop body is captured on
 };

@@ -210,6 +210,8 @@ static void free_problem(asyrk_problem *p)
     if (p->h_out) cudaFreeHost(p->h_out);
     if (p->ev[0]) cudaEventDestroy(p->ev[0]);
     if (p->ev[1]) cudaEventDestroy(p->ev[1]);
+    cudaFree(p->loop_state);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
 }

@@ -123,6 +123,7 @@ int launch_project(const ProjectLaunch &L)
     a.update = L.update;
     a.busy = p->busy;
     a.skipped = p->skipped;
+    a.dyn = L.dyn;
     if (L.sequential) {
         a.workers = 1;
         k<<<1, 32, 0, L.stream>>>(a);

@@ -108,7 +108,7 @@ static int convert(asyrk_problem *p, const void *src, bool src_f64, void *dst, b
     return st;
 }
 
-static bool diverged(double meas, double meas0)
+__host__ __device__ static bool diverged(double meas, double meas0)
 {
     return !isfinite(meas) || meas > 1e30 * (meas0 > 0.0 ? meas0 : 1.0);
 }
@@ -120,7 +120,8 @@ static bool diverged(double meas, double meas0)
 // sweeps done so far -- so a solve stops at most 10 % past the sweep where the
 // tolerance was met, and checks O(log sweeps) times when the decay is steady.
 // Without a measured contraction the interval is one sweep.
-static int64_t next_check(double prev, double meas, int64_t k, int64_t done, double tol)
+__host__ __device__ static int64_t next_check(double prev, double meas, int64_t k, int64_t done,
+                                              double tol)
 {
     int64_t cap = done / 10;
     if (cap < 1) cap = 1;
@@ -134,6 +135,126 @@ static int64_t next_check(double prev, double meas, int64_t k, int64_t done, dou
     if (next < 1.0) next = 1.0;
     if (next > (double)cap) next = (double)cap;
     return (int64_t)next;
+}
+
+// ---------------------------------------------------------------------------
+// graph-captured solve loop: one CUDA-graph launch runs [k sweeps, the check,
+// the decision] in a WHILE node until the decision kernel clears the
+// condition, so the host waits once per solve instead of once per check
+// ---------------------------------------------------------------------------
+struct LoopState {
+    unsigned long long j, count;  // read by the projection kernel (position, length)
+    long long sweeps, k;          // sweeps done, sweeps in the coming launch
+    double meas, meas0, meas_prev;
+    int status, iters;
+};
+static_assert(sizeof(LoopState) == 8 * sizeof(double), "fits the pinned readback buffer");
+
+__global__ void k_loop_decide(LoopState *st, const double *red_out, int kind, double ref,
+                              double tol, long long m, long long max_sweeps, long long check_every,
+                              cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double v = red_out[0];
+    const double meas = kind == MEAS_NORMAL ? v : sqrt(v) / ref;
+    st->j += st->count;
+    st->sweeps += st->k;
+    st->iters += 1;
+    int status = ASYRK_NOT_CONVERGED;
+    if (diverged(meas, st->meas0)) status = ASYRK_DIVERGED;
+    else if (tol > 0.0 && meas <= tol) status = ASYRK_OK;
+    long long next = check_every > 0 ? check_every
+                                     : next_check(st->meas_prev, meas, st->k, st->sweeps, tol);
+    const long long left = max_sweeps - st->sweeps;
+    if (next > left) next = left;
+    st->meas = meas;
+    st->meas_prev = meas;
+    st->status = status;
+    st->k = next;
+    st->count = (unsigned long long)next * (unsigned long long)m;
+    cudaGraphSetConditional(h, (status == ASYRK_NOT_CONVERGED && left > 0) ? 1u : 0u);
+}
+
+static int loop_resources(asyrk_problem *p)
+{
+    if (!p->loop_state) {
+        ASYRK_CK(cudaMalloc(&p->loop_state, sizeof(LoopState)));
+        p->dev_bytes += (int64_t)sizeof(LoopState);
+    }
+    if (!p->cap_stream) ASYRK_CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    return ASYRK_OK;
+}
+
+// Runs the loop from the state in *init (meas0 and the first k set) and
+// returns the final state.  L describes the projection launch (its j0/count
+// are replaced by the device words).
+static int run_device_loop(SolveCtx &c, ProjectLaunch L, const LoopState &init, double tol,
+                           int64_t max_sweeps, int64_t check_every, LoopState *out,
+                           int64_t *launches_per_iter)
+{
+    asyrk_problem *p = c.p;
+    int st = loop_resources(p);
+    if (st != ASYRK_OK) return st;
+    LoopState *dev = (LoopState *)p->loop_state;
+    memcpy(p->h_out, &init, sizeof init);
+    ASYRK_CK(cudaMemcpyAsync(dev, p->h_out, sizeof init, cudaMemcpyHostToDevice, c.s));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto done = [&](int code) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (g) cudaGraphDestroy(g);
+        return code;
+    };
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return done(cuda_fail(e, "cudaGraphCreate", __FILE__, __LINE__));
+    cudaGraphConditionalHandle handle;
+    e = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return done(cuda_fail(e, "cudaGraphConditionalHandleCreate", __FILE__, __LINE__));
+    // cudaGraphNodeParams has no usable default constructor in C++: zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char storage[sizeof(cudaGraphNodeParams)];
+    memset(storage, 0, sizeof storage);
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(storage);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) return done(cuda_fail(e, "cudaGraphAddNode", __FILE__, __LINE__));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(p->cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return done(cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__));
+    const int64_t l0 = p->launches;
+    L.dyn = &dev->j;
+    L.stream = p->cap_stream;
+    st = launch_project(L);
+    if (st == ASYRK_OK) {
+        st = c.kind == MEAS_ERR   ? launch_err2(p, L.x, L.x_f64, p->xt64, 0, p->cap_stream)
+             : c.kind == MEAS_RES ? launch_residual(p, L.x, L.x_f64, false, 0, p->cap_stream)
+                                  : launch_normal_residual(p, L.x, L.x_f64, 0, p->cap_stream);
+    }
+    if (st == ASYRK_OK) {
+        k_loop_decide<<<1, 1, 0, p->cap_stream>>>(dev, p->red_out, c.kind, c.ref, tol,
+                                                  (long long)p->m, (long long)max_sweeps,
+                                                  (long long)check_every, handle);
+        p->launches += 1;
+        if (cudaGetLastError() != cudaSuccess) st = set_error(ASYRK_ECUDA, "decision kernel launch");
+    }
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(p->cap_stream, &captured);
+    if (st != ASYRK_OK) return done(st);
+    if (e != cudaSuccess) return done(cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__));
+    *launches_per_iter = p->launches - l0;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    if (e != cudaSuccess) return done(cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__));
+    e = cudaGraphLaunch(exec, c.s);
+    if (e != cudaSuccess) return done(cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__));
+    e = cudaMemcpyAsync(p->h_out, dev, sizeof(LoopState), cudaMemcpyDeviceToHost, c.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.s);
+    if (e != cudaSuccess) return done(cuda_fail(e, "graph loop", __FILE__, __LINE__));
+    memcpy(out, p->h_out, sizeof *out);
+    return done(ASYRK_OK);
 }
 
 static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps,
@@ -180,6 +301,45 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
     const bool adaptive = o.check_every == 0;
     int64_t k_next = 1;
     double meas_prev = meas0;
+    // the device-driven loop, unless asked for the host loop, per-launch timing,
+    // or shuffled sweeps (which launch sweep by sweep)
+    if (status == ASYRK_NOT_CONVERGED && max_sweeps > 0 && !o.host_loop && !c.profile &&
+        o.sampling == ASYRK_SAMPLE_WEIGHTED) {
+        ProjectLaunch L;
+        L.p = p;
+        L.x = p->xw;
+        L.x_f64 = x_f64;
+        L.gamma = gamma;
+        L.stream_id = 0;
+        L.workers = (int)W;
+        L.subwarp = G;
+        L.sequential = seq;
+        L.exclusive = o.row_exclusion >= 0;
+        L.sampling = o.sampling;
+        L.update = o.update;
+        L.b_from_rec = !x_f64;
+        LoopState init;
+        memset(&init, 0, sizeof init);
+        init.k = adaptive ? 1 : (o.check_every < max_sweeps ? o.check_every : max_sweeps);
+        init.j = p->j_next;
+        init.count = (unsigned long long)init.k * m;
+        init.meas = init.meas0 = init.meas_prev = meas0;
+        init.status = ASYRK_NOT_CONVERGED;
+        L.j0 = init.j;          // the kernel reads both from the loop state; a non-zero
+        L.count = init.count;   // count keeps launch_project from skipping the launch
+        LoopState fin;
+        int64_t per_iter = 0;
+        const int64_t l_before = p->launches;
+        if ((st = run_device_loop(c, L, init, tol, max_sweeps, o.check_every, &fin, &per_iter)) !=
+            ASYRK_OK)
+            return st;
+        p->launches = l_before + per_iter * fin.iters;
+        p->j_next = fin.j;
+        sweeps = fin.sweeps;
+        info.projections += (int64_t)(fin.j - init.j);
+        status = fin.status;
+        meas = fin.meas;
+    }
     while (status == ASYRK_NOT_CONVERGED && sweeps < max_sweeps) {
         int64_t k = adaptive ? k_next : o.check_every;
         if (k > max_sweeps - sweeps) k = max_sweeps - sweeps;
@@ -343,7 +503,7 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
         return set_error(ASYRK_EINVAL, "unknown sampling %d", o.sampling);
     if (o.update < ASYRK_UPDATE_ROW || o.update > ASYRK_UPDATE_SINGLE)
         return set_error(ASYRK_EINVAL, "unknown update %d", o.update);
-    if (o.reserved3 != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
+    if (o.host_loop < 0 || o.host_loop > 1) return set_error(ASYRK_EINVAL, "host_loop must be 0 or 1");
     if (o.mode == ASYRK_MODE_SEQUENTIAL && o.workers > 1)
         return set_error(ASYRK_EINVAL, "SEQUENTIAL mode has one worker");
 

@@ -42,6 +42,7 @@ struct ProjArgs {
     int update;                      // 0: the whole row, 1: one coordinate (Algorithm 1)
     unsigned *busy;                  // row-claim bits (row exclusion)
     unsigned long long *skipped;     // projections skipped by row exclusion
+    const unsigned long long *dyn;   // non-null: j0 = dyn[0], count = dyn[1] (device loop)
 };
 
 // ---- streamed row loads: read once per projection, so marked evict-first --
@@ -147,7 +148,7 @@ __device__ __forceinline__ void release_row(unsigned *busy, unsigned i)
                  : "memory");
 }
 
-template <typename VT, typename XT, int G, bool SEQ, bool EXCL>
+template <typename VT, typename XT, int G, bool SEQ, bool EXCL, bool DYN = true>
 __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, long long gbase,
                                                           long long W)
 {
@@ -164,19 +165,29 @@ __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, lon
     const XT gamma = (XT)a.gamma;
     unsigned long long skipped = 0;
 
+    // the launch's position and length: arguments, or device words that a
+    // graph-captured loop advances between launches
+    unsigned long long dj0 = 0, dcount = 0;
+    if (DYN) {
+        dj0 = a.dyn ? __ldcg(a.dyn) : a.j0;
+        dcount = a.dyn ? __ldcg(a.dyn + 1) : a.count;
+    }
+#define ASYRK_J0 (DYN ? dj0 : a.j0)
+#define ASYRK_COUNT (DYN ? dcount : a.count)
+
     // t0 walks k*W + gbase, so worker gbase+sub gets projection t0 + sub.  The
     // trip count is warp-uniform: every lane reaches every shuffle and barrier.
-    for (unsigned long long t0 = (unsigned long long)gbase; t0 < a.count;
+    for (unsigned long long t0 = (unsigned long long)gbase; t0 < ASYRK_COUNT;
          t0 += (unsigned long long)W) {
         const unsigned long long t = t0 + sub;
-        bool act = worker && t < a.count;
+        bool act = worker && t < ASYRK_COUNT;
         long long start = 0;
         int len = 0;
         unsigned i = 0, pick = 0;
         XT b = 0, scale = 0;
         if (act) {
             RowRec r;
-            const unsigned long long j = a.j0 + t;
+            const unsigned long long j = ASYRK_J0 + t;
             if (a.sampling == 1) {
                 i = shuffled_position(j, a.m, a.stream_id, a.key, a.shuf_h);
                 r = load_rec(a.rec + i);
@@ -274,6 +285,8 @@ __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, lon
         }
     }
     return skipped;
+#undef ASYRK_J0
+#undef ASYRK_COUNT
 }
 
 }  // namespace asyrk
