@@ -157,10 +157,11 @@ typedef struct asyrk_solve_opts {
     int32_t measure;         /* asyrk_measure of the convergence check               */
     int32_t sampling;        /* asyrk_sampling of the row sequence                   */
     int32_t update;          /* asyrk_update                                         */
-    int32_t host_loop;       /* 0: SEQUENTIAL/ASYNC solves with weighted sampling and
+    int32_t graph_loop;      /* 1: SEQUENTIAL/ASYNC solves with weighted sampling and
                                 profile = 0 run their sweep-check loop inside one
-                                CUDA graph (a WHILE node; the host waits once);
-                                1: the host drives the loop (one wait per check) */
+                                CUDA graph (a WHILE node; the host waits once per
+                                solve); 0 (default): the host drives the loop, one
+                                wait per check                                      */
 } asyrk_solve_opts;
 
 typedef struct asyrk_solve_info {

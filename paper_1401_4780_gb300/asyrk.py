@@ -52,7 +52,7 @@ class SolveOpts(ctypes.Structure):
                 ("inner_sweeps", ctypes.c_int64), ("profile", ctypes.c_int32),
                 ("row_exclusion", ctypes.c_int32), ("measure", ctypes.c_int32),
                 ("sampling", ctypes.c_int32), ("update", ctypes.c_int32),
-                ("host_loop", ctypes.c_int32)]
+                ("graph_loop", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -447,12 +447,12 @@ def asyrk_problem_get_stats(h):
 # ---------------------------------------------------------------------------
 def solve_opts(mode=MODE_ASYNC, workers=0, subwarp=0, check_every=1, x_true=None, stream=None,
                inner_tol=0.0, inner_sweeps=0, profile=False, device_ptrs=False, row_exclusion=0,
-               measure=MEASURE_AUTO, sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW, host_loop=False):
+               measure=MEASURE_AUTO, sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW, graph_loop=False):
     return SolveOpts(mode=mode, device_ptrs=1 if device_ptrs else 0, workers=workers,
                      subwarp=subwarp, check_every=check_every, x_true=_ptr(x_true),
                      stream=_stream(stream), inner_tol=inner_tol, inner_sweeps=inner_sweeps,
                      profile=1 if profile else 0, row_exclusion=row_exclusion, measure=measure,
-                     sampling=sampling, update=update, host_loop=1 if host_loop else 0)
+                     sampling=sampling, update=update, graph_loop=1 if graph_loop else 0)
 
 
 class Problem:

@@ -301,9 +301,9 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
     const bool adaptive = o.check_every == 0;
     int64_t k_next = 1;
     double meas_prev = meas0;
-    // the device-driven loop, unless asked for the host loop, per-launch timing,
-    // or shuffled sweeps (which launch sweep by sweep)
-    if (status == ASYRK_NOT_CONVERGED && max_sweeps > 0 && !o.host_loop && !c.profile &&
+    // the device-driven loop when asked for, except with per-launch timing or
+    // shuffled sweeps (which launch sweep by sweep)
+    if (status == ASYRK_NOT_CONVERGED && max_sweeps > 0 && o.graph_loop && !c.profile &&
         o.sampling == ASYRK_SAMPLE_WEIGHTED) {
         ProjectLaunch L;
         L.p = p;
@@ -503,7 +503,7 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
         return set_error(ASYRK_EINVAL, "unknown sampling %d", o.sampling);
     if (o.update < ASYRK_UPDATE_ROW || o.update > ASYRK_UPDATE_SINGLE)
         return set_error(ASYRK_EINVAL, "unknown update %d", o.update);
-    if (o.host_loop < 0 || o.host_loop > 1) return set_error(ASYRK_EINVAL, "host_loop must be 0 or 1");
+    if (o.graph_loop < 0 || o.graph_loop > 1) return set_error(ASYRK_EINVAL, "graph_loop must be 0 or 1");
     if (o.mode == ASYRK_MODE_SEQUENTIAL && o.workers > 1)
         return set_error(ASYRK_EINVAL, "SEQUENTIAL mode has one worker");
 

@@ -1,5 +1,6 @@
-"""The graph-captured solve loop (one CUDA-graph launch runs sweeps, checks and
-the stop decision in a WHILE node) against the host-driven loop.
+"""The graph-captured solve loop (graph_loop = 1: one CUDA-graph launch runs
+sweeps, checks and the stop decision in a WHILE node) against the host-driven
+loop (the default).
 
   * SEQUENTIAL: the same kernels in the same order, so the same iterate bit for
     bit, the same sweep count and the same final position;
@@ -26,19 +27,19 @@ def gpu():
     asyrk.load()
 
 
-def _solve(p, s, host_loop, **kw):
+def _solve(p, s, graph_loop, **kw):
     p.position = 0
     x = np.zeros(s.n)
-    st, info = p.solve(x, host_loop=host_loop, **kw)
+    st, info = p.solve(x, graph_loop=graph_loop, **kw)
     return st, info, x, p.position
 
 
 def test_sequential_is_identical_in_both_loops():
     s = synth.plain_f64_system()
     with asyrk.Problem.from_system(s) as p:
-        a = _solve(p, s, False, tol=1e-6, max_sweeps=50, mode=asyrk.MODE_SEQUENTIAL,
+        a = _solve(p, s, True, tol=1e-6, max_sweeps=50, mode=asyrk.MODE_SEQUENTIAL,
                    x_true=s.x_true)
-        b = _solve(p, s, True, tol=1e-6, max_sweeps=50, mode=asyrk.MODE_SEQUENTIAL,
+        b = _solve(p, s, False, tol=1e-6, max_sweeps=50, mode=asyrk.MODE_SEQUENTIAL,
                    x_true=s.x_true)
     assert a[0] == b[0] == asyrk.OK
     assert a[1].sweeps == b[1].sweeps and a[3] == b[3]
@@ -57,8 +58,8 @@ def test_async_reaches_tolerance_in_both_loops(measure, every):
         kw = dict(tol=1e-5, x_true=s.x_true if measure == "error" else None,
                   measure=asyrk.MEASURE_RESIDUAL if measure == "residual" else asyrk.MEASURE_AUTO)
     with asyrk.Problem.from_system(s) as p:
-        dev = _solve(p, s, False, max_sweeps=3000, check_every=every, **kw)
-        host = _solve(p, s, True, max_sweeps=3000, check_every=every, **kw)
+        dev = _solve(p, s, True, max_sweeps=3000, check_every=every, **kw)
+        host = _solve(p, s, False, max_sweeps=3000, check_every=every, **kw)
     for st, info, x, pos in (dev, host):
         assert st == asyrk.OK, info.as_dict()
         assert pos == info.projections
@@ -76,9 +77,9 @@ def test_async_reaches_tolerance_in_both_loops(measure, every):
 def test_sweep_limits_in_the_graph_loop():
     s = synth.plain_f64_system()
     with asyrk.Problem.from_system(s) as p:
-        st, info, x, pos = _solve(p, s, False, tol=1e-30, max_sweeps=7, x_true=s.x_true)
+        st, info, x, pos = _solve(p, s, True, tol=1e-30, max_sweeps=7, x_true=s.x_true)
         assert st == asyrk.NOT_CONVERGED and info.sweeps == 7 and pos == 7 * s.m
-        st, info, x, pos = _solve(p, s, False, tol=0.0, max_sweeps=5, check_every=2)
+        st, info, x, pos = _solve(p, s, True, tol=0.0, max_sweeps=5, check_every=2)
         assert st == asyrk.OK and info.sweeps == 5 and pos == 5 * s.m
-        st, info, x, pos = _solve(p, s, False, tol=1e-8, max_sweeps=0)
+        st, info, x, pos = _solve(p, s, True, tol=1e-8, max_sweeps=0)
         assert info.sweeps == 0 and pos == 0 and not np.any(x)
