@@ -402,6 +402,36 @@ def extras_table2(asyrk, synth, torch):
             "rows": rows}
 
 
+def extras_tau_threshold(asyrk, synth):
+    """Corollary 2's delay bound on a small system (m=4096, n=1024, 16 nnz/row, unit
+    rows, FP32; to ||x-x*||/||x*|| <= 1e-6): the automatic worker count is the
+    bound's estimate m/(2e(1+sqrt(m/n))^2) - 1; multiples of it show where the
+    asynchronous iteration stops converging."""
+    s = synth.make_system(4096, 1024, 16, synth.config_seed(3), row_norms="unit",
+                          value_dtype="f32")
+    rows = []
+    with asyrk.Problem.from_system(s) as p:
+        x = np.zeros(s.n)
+        st, info = p.solve(x, tol=1e-6, max_sweeps=2000, x_true=s.x_true)
+        w0 = info.workers
+        for mult in (1, 2, 3, 6, 12, 48):
+            best = None
+            for rep in range(3):
+                p.position = 0
+                x = np.zeros(s.n)
+                st, info = p.solve(x, tol=1e-6, max_sweeps=2000, x_true=s.x_true,
+                                   workers=w0 * mult)
+                if best is None or info.seconds < best[1].seconds:
+                    best = (st, info)
+            st, info = best
+            rows.append({"workers": info.workers, "multiple_of_bound": mult, "status": st,
+                         "sweeps": info.sweeps, "ms": 1e3 * info.seconds,
+                         "skipped_fraction": info.skipped / max(1, info.projections)})
+    return {"workload": "m=4096, n=1024, 16 nnz/row, unit rows, FP32, tol 1e-6; workers as "
+                        "multiples of Corollary 2's estimate (the automatic count); status 0 "
+                        "converged, 2 diverged", "rows": rows}
+
+
 def extras_tau_study(asyrk, synth, torch):
     """Figures 1-2 on the GPU: m=80000, n=100000, delta = 0.001 and 0.003, gamma = 1;
     epochs (n projections) to ||Ax - b||/||b|| <= 1e-4 and time, for a range of worker
@@ -814,6 +844,7 @@ def run_asyrk(args, dist):
                   "table2": extras_table2(asyrk, synth, torch),
                   "least_squares": extras_lsq(asyrk, synth, torch),
                   "tau_study": extras_tau_study(asyrk, synth, torch),
+                  "tau_threshold": extras_tau_threshold(asyrk, synth),
                   "batched": extras_batched(asyrk, synth, torch),
                   "served": extras_served(asyrk, synth, torch, args.served_seconds,
                                           args.served_rate)}
