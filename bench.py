@@ -574,6 +574,10 @@ def extras_batched(asyrk, synth, torch):
         proj_plain += ip.projections - ip.skipped
         ok_plain += stp == asyrk.OK
     sweeps = [i.sweeps for i in infos]
+    # algorithmic bytes: each projection streams its row (4 B column + 4 B value per
+    # nonzero) and its 32 B record; per system, its projections x its row length
+    alg_bytes = sum(i.projections * (8 * L + 32) for i, (m, n, L) in zip(infos, shapes))
+    peak, peak_kind = read_peaks()
     out = {"workload": "256 systems: m = floor(2^U(11,18)), n = m/4, nnz/row U{8..64} per system, "
                        "N(0,1) values, unit rows, FP32; each to ||x-x*||/||x*|| <= 1e-6",
            "systems": len(shapes), "sum_m": int(sum(m for m, _, _ in shapes)),
@@ -581,6 +585,9 @@ def extras_batched(asyrk, synth, torch):
            "converged": bi.converged, "iterations": bi.iterations, "graph_launch": bool(bi.graph),
            "device_ms": bi.device_ms, "wall_ms": 1e3 * bi.seconds,
            "projections_per_s": bi.projections / (bi.device_ms / 1e3),
+           "row_stream_gbs": alg_bytes / (bi.device_ms / 1e3) / 1e9,
+           "row_stream_frac_of_hbm": alg_bytes / (bi.device_ms / 1e3) / 1e9 / peak,
+           "hbm_peak_source": peak_kind,
            "max_rel_err_host": max(errs), "sweeps_median": float(np.median(sweeps)),
            "sweeps_max": int(max(sweeps)), "kernel_launches": bi.kernel_launches,
            "resident_warps": bi.resident_warps, "autotuned_by_row_length_class": tuned,
