@@ -125,3 +125,45 @@ def test_autotune_shape_is_used_by_solve():
         x = np.zeros(s.n)
         st, info = p.solve(x, tol=1e-5, max_sweeps=400, x_true=s.x_true)
         assert st == asyrk.OK and info.subwarp == r.subwarp
+
+
+def test_full_batched_workload():
+    """The 256-system workload the benchmark times (m = 2^11..2^18 log-uniform,
+    n = m/4, 8..64 entries per row, FP32; 560 M nonzeros in all), in one graph
+    launch: every system reaches 1e-6 (checked against x* in FP64 on the GPU by
+    torch, independently of the library), and the smallest systems need no more
+    than 1.5x the oracle's median sweep count."""
+    import torch
+    shapes = synth.batch_shapes()
+    base = synth.config_seed(4) * 1000
+    probs, xts, small = [], [], []
+    smallest = set(sorted(range(len(shapes)), key=lambda k: shapes[k][0])[:3])
+    for k, (m, n, L) in enumerate(shapes):
+        d = synth.make_system_torch(m, n, L, base + k, row_norms="unit", value_dtype="f32")
+        torch.cuda.synchronize()
+        probs.append(asyrk.Problem(m, n, d["row_ptr"], d["col"], d["val_store"], asyrk.F32,
+                                   d["b"], seed=synth.solver_seed(base + k), device_ptrs=True))
+        xts.append(d["x_true"])
+        if k in smallest:
+            small.append((k, {key: d[key].cpu().numpy() for key in ("row_ptr", "col", "val_store",
+                                                                    "b", "x_true")}))
+        del d
+    xs = [torch.zeros(p.n, dtype=torch.float64, device="cuda") for p in probs]
+    with asyrk.Batch(probs) as b:
+        st, infos, bi = b.solve(xs, tols=[1e-6] * len(xs), max_sweeps=400, x_trues=xts,
+                                device_ptrs=True)
+    assert st == asyrk.OK and bi.converged == len(shapes) and bi.graph == 1
+    errs = [float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)) for x, xt in zip(xs, xts)]
+    assert max(errs) <= 1e-6, max(errs)
+    for k, h in small:
+        m, n, L = shapes[k]
+        val64 = h["val_store"].astype(np.float64)
+        sweeps = []
+        for rep in range(3):
+            xo = np.zeros(n)
+            r = oracle.rk_solve(m, n, h["row_ptr"], h["col"], val64, h["b"], xo, 1.0,
+                                synth.solver_seed(base + k) + rep, 1e-6, 400, x_true=h["x_true"])
+            sweeps.append(r.sweeps)
+        assert infos[k].sweeps <= 1.5 * np.median(sweeps), (m, infos[k].sweeps, sweeps)
+    for p in probs:
+        p.close()
