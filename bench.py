@@ -171,6 +171,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gpu_local_cpus(dev):
+    """The CPUs sysfs lists as local to the GPU's PCI device, among those this
+    process may use (None when unknown)."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/local_cpulist" % bus) as f:
+            text = f.read().strip()
+    except (AttributeError, OSError, RuntimeError):
+        return None
+    cpus = set()
+    for part in text.split(","):
+        if "-" in part:
+            lo, hi = part.split("-")
+            cpus.update(range(int(lo), int(hi) + 1))
+        elif part:
+            cpus.add(int(part))
+    local = cpus & os.sched_getaffinity(0)
+    return local or None
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -705,6 +727,14 @@ def run_asyrk(args, dist):
 
     assert torch.cuda.is_available(), "bench.py needs a GPU"
     torch.cuda.set_device(dist.local_rank)
+    # host buffers (pinned inputs of the end-to-end leg) on the GPU's side of the
+    # host: run on the CPUs local to it while the GPU legs run
+    all_cpus = os.sched_getaffinity(0)
+    local = gpu_local_cpus(dist.local_rank)
+    if local and local != all_cpus:
+        os.sched_setaffinity(0, local)
+    affinity = {"gpu_local_cpus": len(local) if local else None, "cpus": len(all_cpus),
+                "pinned_to_local": bool(local and local != all_cpus)}
     asyrk.load()
     s = make_workload(dist.rank, args.scale)
     seed = synth.solver_seed(s.seed)
@@ -833,11 +863,13 @@ def run_asyrk(args, dist):
     e2e = None if args.e2e_steps <= 0 else {"value": e2e_proj / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h),
            "what": "asyrk_create from pinned host CSR + asyrk_solve (host x0 -> host x) + destroy",
-           "ms_per_step_split": {k: 1e3 * v / max(1, args.e2e_steps) for k, v in split.items()}}
+           "ms_per_step_split": {k: 1e3 * v / max(1, args.e2e_steps) for k, v in split.items()},
+           "host_affinity": affinity}
 
     cpu = None
     cpu_mt = None
     if dist.rank == 0 and dist.world == 1 and args.cpu_seconds > 0:
+        os.sched_setaffinity(0, all_cpus)  # the CPU baselines get every core again
         rate, nsteps, dt = cpu_oracle_sample(s, args.gamma, args.cpu_seconds, seed)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d projections (%.2f sweeps) of the same system from x0=0, FP64 "

@@ -48,7 +48,7 @@ def run(m, row_ptr, col, val, b, x, gamma=1.0, threads=None, scans=1, seed=1):
     """Runs ``scans`` scans of every thread's row slice; x (float32) is updated in place.
 
     Returns (projections, seconds, threads)."""
-    threads = threads or os.cpu_count() or 1
+    threads = threads or len(os.sched_getaffinity(0)) or 1
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     c = np.ascontiguousarray(col, dtype=np.int32)
     v = np.ascontiguousarray(val, dtype=np.float32)
