@@ -102,3 +102,29 @@ def test_create_rejects_null_arrays_and_bad_dtype(lib):
 def test_solve_rejects_null_handle(lib):
     st, info = asyrk.asyrk_solve(None, np.zeros(1), 1.0, 1e-6, 1)
     assert st == asyrk.EINVAL and info.status == 0
+
+
+def test_argument_errors_need_no_gpu():
+    """Arguments are checked before any CUDA call: these return EINVAL on a host
+    without a GPU (and without creating a CUDA context)."""
+    rp = np.array([0, 1], dtype=np.int64)
+    col = np.array([0], dtype=np.int32)
+    val = np.array([1.0])
+    b = np.array([1.0])
+    for m, n in [(0, 1), (1, 0), (-3, 4), (2**31, 1), (1, 2**31)]:
+        st, h = asyrk.asyrk_create(m, n, rp, col, val, asyrk.F64, b)
+        assert st == asyrk.EINVAL and not h.value
+    st, h = asyrk.asyrk_create(1, 1, rp, col, val, 7, b)  # unknown dtype
+    assert st == asyrk.EINVAL and not h.value
+    st, h = asyrk.asyrk_create(1, 1, None, col, val, asyrk.F64, b)
+    assert st == asyrk.EINVAL and not h.value
+    st, h = asyrk.asyrk_lsq_create(1, 1, rp, col, val, asyrk.F64, b, -1.0)
+    assert st == asyrk.EINVAL and not h.value
+    st, h = asyrk.asyrk_lsq_create(2**30, 2**30, rp, col, val, asyrk.F64, b, 1.0)
+    assert st == asyrk.EINVAL and not h.value  # m + n > 2^31 - 1
+    st, lo, hi = asyrk.asyrk_spectrum_estimate(1, 1, rp, col, val, asyrk.F64, steps=-1)
+    assert st == asyrk.EINVAL
+    st, info = asyrk.asyrk_solve(ctypes.c_void_p(), np.zeros(1), 1.0, 1e-6, 10)
+    assert st == asyrk.EINVAL
+    assert asyrk.asyrk_lsq_solution(ctypes.c_void_p(), np.zeros(1), np.zeros(1)) == asyrk.EINVAL
+    assert asyrk.load().asyrk_strerror(asyrk.EINVAL)
