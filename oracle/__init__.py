@@ -310,3 +310,30 @@ def mu_nu(m, n, row_ptr, col):
     mu = int(np.max(np.diff(rp)))
     nu = int(np.max(np.bincount(np.asarray(col), minlength=n)))
     return mu, nu
+
+
+# --------------------------------------------------------------------------
+# Step-length theory (Theorem 2, Corollary 2): formulas for reports and tests
+# --------------------------------------------------------------------------
+def theorem2_psi(mu, lmax, m, tau, rho):
+    """psi = mu + 2 lambda_max tau rho^tau / m (the quantity of Theorem 2)."""
+    return mu + 2.0 * lmax * tau * rho ** tau / m
+
+
+def theorem2_step_bounds(mu, alpha, lmax, m, tau, rho):
+    """The three upper bounds Theorem 2 puts on gamma: 1/psi,
+    m (rho - 1) / (2 lambda_max rho^(tau+1)) and
+    m sqrt((rho - 1) / (rho^tau (m alpha^2 + lambda_max^2 tau rho^tau)))."""
+    psi = theorem2_psi(mu, lmax, m, tau, rho)
+    b1 = 1.0 / psi
+    b2 = m * (rho - 1.0) / (2.0 * lmax * rho ** (tau + 1))
+    b3 = m * np.sqrt((rho - 1.0) / (rho ** tau * (m * alpha ** 2 + lmax ** 2 * tau * rho ** tau)))
+    return b1, b2, b3
+
+
+def corollary2(mu, lmax, m, tau):
+    """(rho, psi, gamma) of Corollary 2: rho = 1 + 2 e lambda_max (tau + 1) / m,
+    gamma = 1/psi; its assumption is 2 e lambda_max (tau + 1) / m <= 1."""
+    rho = 1.0 + 2.0 * np.e * lmax * (tau + 1) / m
+    psi = theorem2_psi(mu, lmax, m, tau, rho)
+    return rho, psi, 1.0 / psi
