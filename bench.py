@@ -73,6 +73,10 @@ def parse_args():
     ap.add_argument("--served-rate", type=float, default=2000.0, help="requests per second")
     ap.add_argument("--served-rate2", type=float, default=1000.0,
                     help="a second, lower offered rate (0: skip)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="profiling aid: run only the 256-system batched case, print its JSON")
+    ap.add_argument("--batch-host-loop", action="store_true",
+                    help="with --batched-only: host-driven engine loop (separate launches)")
     return ap.parse_args()
 
 
@@ -556,7 +560,7 @@ def extras_lsq(asyrk, synth, torch):
             "normal_eq_rel_residual": opt}
 
 
-def extras_batched(asyrk, synth, torch):
+def extras_batched(asyrk, synth, torch, graph=True):
     shapes = synth.batch_shapes()
     base = synth.config_seed(4) * 1000
     probs, x_trues = [], []
@@ -580,7 +584,7 @@ def extras_batched(asyrk, synth, torch):
                          "projections_per_s": r.projections_per_s, "trials": r.trials}
     xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for (_, n, _) in shapes]
     tols = [1e-6] * len(shapes)
-    with asyrk.Batch(probs) as b:
+    with asyrk.Batch(probs, graph=graph) as b:
         b.solve(xs, tols=tols, max_sweeps=400, x_trues=x_trues, device_ptrs=True)  # warm-up
         for x in xs:
             x.zero_()
@@ -914,6 +918,13 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.batched_only:
+            import torch
+            from paper_1401_4780_gb300 import asyrk, synth
+            torch.cuda.set_device(dist.local_rank)
+            asyrk.load()
+            print(json.dumps(extras_batched(asyrk, synth, torch, graph=not args.batch_host_loop)),
+                  flush=True)
         else:
             run_asyrk(args, dist)
     finally:
