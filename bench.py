@@ -175,6 +175,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gpu_numa_node(dev):
+    """The NUMA node sysfs gives for the GPU's PCI device (None when unknown)."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/numa_node" % bus) as f:
+            node = int(f.read().strip())
+        return node if node >= 0 else None
+    except (AttributeError, OSError, RuntimeError, ValueError):
+        return None
+
+
+def cpu_numa_nodes(cpus):
+    """The NUMA nodes of the given CPUs (from sysfs), as a sorted list."""
+    nodes = set()
+    for c in cpus:
+        try:
+            for name in os.listdir("/sys/devices/system/cpu/cpu%d" % c):
+                if name.startswith("node") and name[4:].isdigit():
+                    nodes.add(int(name[4:]))
+        except OSError:
+            pass
+    return sorted(nodes)
+
+
 def gpu_local_cpus(dev):
     """The CPUs sysfs lists as local to the GPU's PCI device, among those this
     process may use (None when unknown)."""
@@ -738,7 +764,9 @@ def run_asyrk(args, dist):
     if local and local != all_cpus:
         os.sched_setaffinity(0, local)
     affinity = {"gpu_local_cpus": len(local) if local else None, "cpus": len(all_cpus),
-                "pinned_to_local": bool(local and local != all_cpus)}
+                "pinned_to_local": bool(local and local != all_cpus),
+                "gpu_numa_node": gpu_numa_node(dist.local_rank),
+                "cpu_numa_nodes": cpu_numa_nodes(all_cpus)}
     asyrk.load()
     s = make_workload(dist.rank, args.scale)
     seed = synth.solver_seed(s.seed)
