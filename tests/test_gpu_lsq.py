@@ -208,3 +208,21 @@ def test_bad_arguments_are_refused():
     s = synth.plain_f64_system()
     with asyrk.Problem.from_system(s) as p:
         assert asyrk.asyrk_lsq_solution(p.h, np.zeros(s.n), np.zeros(s.n)) == asyrk.EINVAL
+
+
+def test_bf16_values_refined_least_squares_device_pointers():
+    """BF16-stored A (the stored values are A), FP64 refinement, every array on the
+    device, zeta estimated: x_LS of the stored matrix to 1e-9 (numpy lstsq)."""
+    import torch
+    s, b, A, x_ls, sr = _inconsistent(3000, 1000, 12, 74, "bf16")
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with asyrk.Problem.lsq(s.m, s.n, d(s.row_ptr), d(s.col), d(s.val_store), "bf16", d(b),
+                           seed=11, device_ptrs=True) as p:
+        zeta, _ = p.lsq_params()
+        assert 0.9 * sr / np.sqrt(2) <= zeta <= 1.02 * sr / np.sqrt(2)  # BF16-rounded estimate
+        z = torch.zeros(s.n + s.m, dtype=torch.float64, device="cuda")
+        st, info = p.solve(z, tol=1e-12, max_sweeps=8000, mode=asyrk.MODE_REFINE,
+                           device_ptrs=True)
+        assert st == asyrk.OK, info.as_dict()
+        x = p.lsq_solution(z, on_device=True).cpu().numpy()
+    assert np.linalg.norm(x - x_ls) <= 1e-9 * np.linalg.norm(x_ls)
