@@ -27,6 +27,7 @@ slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -199,6 +200,49 @@ def cpu_numa_nodes(cpus):
         except OSError:
             pass
     return sorted(nodes)
+
+
+_NODE_PINNED = []  # (address, size) of host buffers bound to a NUMA node and registered
+
+
+def pinned_on_node(arr, node):
+    """A page-locked host copy of arr whose pages live on NUMA node `node` (the GPU's):
+    anonymous memory bound to the node with mbind, filled, then registered with
+    CUDA.  Falls back to torch's pinned allocation when any step is unavailable."""
+    import platform
+    import torch
+    arr = np.ascontiguousarray(arr)
+    nr = {"aarch64": 235, "x86_64": 237}.get(platform.machine())
+    if node is None or nr is None or arr.nbytes == 0:
+        return torch.from_numpy(arr).pin_memory()
+    libc = ctypes.CDLL(None, use_errno=True)
+    libc.mmap.restype = ctypes.c_void_p
+    libc.mmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_int, ctypes.c_long]
+    libc.munmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    page = os.sysconf("SC_PAGE_SIZE")
+    size = (arr.nbytes + page - 1) // page * page
+    addr = libc.mmap(None, size, 3, 0x22, -1, 0)  # PROT_READ|WRITE, MAP_PRIVATE|ANONYMOUS
+    if not addr or addr == ctypes.c_void_p(-1).value:
+        return torch.from_numpy(arr).pin_memory()
+    mask = (ctypes.c_ulong * 16)()
+    mask[node // 64] = 1 << (node % 64)
+    rc = libc.syscall(ctypes.c_long(nr), ctypes.c_void_p(addr), ctypes.c_ulong(size),
+                      ctypes.c_int(2), mask, ctypes.c_ulong(16 * 64 + 1), ctypes.c_uint(0))
+    if rc != 0:  # MPOL_BIND refused
+        libc.munmap(addr, size)
+        return torch.from_numpy(arr).pin_memory()
+    ctypes.memmove(addr, arr.ctypes.data, arr.nbytes)  # first touch, on the node
+    try:
+        ok = int(torch.cuda.cudart().cudaHostRegister(addr, size, 0)) == 0
+    except (AttributeError, RuntimeError, TypeError):
+        ok = False
+    if not ok:
+        libc.munmap(addr, size)
+        return torch.from_numpy(arr).pin_memory()
+    _NODE_PINNED.append((addr, size))
+    buf = (ctypes.c_char * arr.nbytes).from_address(addr)
+    return torch.frombuffer(buf, dtype=torch.from_numpy(arr[:0]).dtype)
 
 
 def gpu_local_cpus(dev):
@@ -862,7 +906,8 @@ def run_asyrk(args, dist):
     p.close()
 
     # ---------------- end to end from host buffers ----------------
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    node = gpu_numa_node(dist.local_rank)
+    pin = lambda a: pinned_on_node(a, node)
     h_rp, h_col, h_val, h_b, h_xt = (pin(s.row_ptr), pin(s.col), pin(s.val_store), pin(s.b),
                                      pin(s.x_true))
     h_x = torch.zeros(s.n, dtype=torch.float64).pin_memory()
