@@ -955,18 +955,27 @@ def run_asyrk(args, dist):
 
     extras = None
     if dist.rank == 0 and not args.no_extras:
+        # each extra measurement is reported on its own: one that fails records its
+        # error instead of taking the benchmark line down with it
+        def guarded(fn, *a):
+            try:
+                return fn(*a)
+            except Exception as exc:  # noqa: BLE001 -- reported, not swallowed
+                torch.cuda.synchronize()
+                return {"error": "%s: %s" % (type(exc).__name__, exc)}
+
         extras = {"gamma_sweep": gamma_sweep,
-                  "plain_and_refine": extras_plain_refine(asyrk, synth),
-                  "table2": extras_table2(asyrk, synth, torch),
-                  "least_squares": extras_lsq(asyrk, synth, torch),
-                  "tau_study": extras_tau_study(asyrk, synth, torch),
-                  "tau_threshold": extras_tau_threshold(asyrk, synth),
-                  "batched": extras_batched(asyrk, synth, torch),
-                  "served": extras_served(asyrk, synth, torch, args.served_seconds,
-                                          args.served_rate)}
+                  "plain_and_refine": guarded(extras_plain_refine, asyrk, synth),
+                  "table2": guarded(extras_table2, asyrk, synth, torch),
+                  "least_squares": guarded(extras_lsq, asyrk, synth, torch),
+                  "tau_study": guarded(extras_tau_study, asyrk, synth, torch),
+                  "tau_threshold": guarded(extras_tau_threshold, asyrk, synth),
+                  "batched": guarded(extras_batched, asyrk, synth, torch),
+                  "served": guarded(extras_served, asyrk, synth, torch, args.served_seconds,
+                                    args.served_rate)}
         if args.served_rate2 > 0:
-            extras["served_lower_rate"] = extras_served(asyrk, synth, torch, args.served_seconds,
-                                                        args.served_rate2)
+            extras["served_lower_rate"] = guarded(extras_served, asyrk, synth, torch,
+                                                  args.served_seconds, args.served_rate2)
 
     if dist.rank == 0:
         cfg = workload_config(s, args)
