@@ -961,7 +961,10 @@ def run_asyrk(args, dist):
             try:
                 return fn(*a)
             except Exception as exc:  # noqa: BLE001 -- reported, not swallowed
-                torch.cuda.synchronize()
+                try:
+                    torch.cuda.synchronize()
+                except Exception:  # noqa: BLE001 -- the error above is the one reported
+                    pass
                 return {"error": "%s: %s" % (type(exc).__name__, exc)}
 
         extras = {"gamma_sweep": gamma_sweep,
