@@ -158,9 +158,7 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
         asyrk_problem *p = problems[k];
         SysDesc &D = b->h[k];
         memset(&D, 0, sizeof D);
-        bool tuned = false;
-        int G = tuned_subwarp(p->dtype, p->max_len, p->nnz, p->m, &tuned);
-        if (!tuned) G = choose_subwarp(p->max_len, p->nnz, p->m);
+        const int G = engine_subwarp(p);
         const long long capw = tau_cap_estimate(p->m, p->n);
         D.G = G;
         long long cw = (capw * G + 31) / 32;

@@ -249,9 +249,7 @@ static bool admit_locked(asyrk_server *sv, Request *r, int k)
     }
     SysDesc &D = sv->h[k];
     memset(&D, 0, sizeof D);
-    bool tuned = false;
-    int G = tuned_subwarp(p->dtype, p->max_len, p->nnz, p->m, &tuned);
-    if (!tuned) G = choose_subwarp(p->max_len, p->nnz, p->m);
+    const int G = engine_subwarp(p);
     const long long capw = tau_cap_estimate(p->m, p->n);
     const long long cw = (capw * G + 31) / 32;
     D.G = G;

@@ -52,6 +52,12 @@ def test_batch_reaches_tolerance_within_oracle_sweeps(graph):
         assert bi.converged == len(systems) and bi.graph == (1 if graph else 0)
         assert bi.iterations == max(i.sweeps for i in infos)
     for s, x, info in zip(systems, xs, infos):
+        if s.value_dtype == "bf16":  # no tuned shape for these: the engine halves the default
+            L = int(np.max(np.diff(s.row_ptr)))
+            G = 2
+            while G < 32 and 4 * G < L:
+                G *= 2
+            assert info.subwarp == max(1, G // 2), (L, info.subwarp)
         assert _err(x, s) <= 1e-6 and abs(info.rel_err - _err(x, s)) <= 1e-3 * _err(x, s)
         assert info.rel_res < 1e-5
         sweeps = []
