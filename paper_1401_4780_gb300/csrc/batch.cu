@@ -158,7 +158,7 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
         asyrk_problem *p = problems[k];
         SysDesc &D = b->h[k];
         memset(&D, 0, sizeof D);
-        const int G = engine_subwarp(p);
+        const int G = engine_subwarp(p, true);
         const long long capw = tau_cap_estimate(p->m, p->n);
         D.G = G;
         long long cw = (capw * G + 31) / 32;

@@ -105,13 +105,15 @@ int launch_batch_outer(SysDesc *d, int count, int total_chunks, double *part, cu
 int choose_subwarp(int64_t max_len, int64_t nnz, int64_t m);
 int tuned_subwarp(int dtype, int64_t max_len, int64_t nnz, int64_t m, bool *found);
 
-// Sub-warp width of a slot in the multi-system engine: half the single-system
-// width (tuned, else the default), at least one lane.  A slot gets a share of
-// the GPU, so its workers are latency-bound rather than L2-bound; twice the rows
-// per warp in flight beat keeping each row in one register chunk (measured on
-// the 256-system batch: 92 ms against 97.5 ms at the full width, 94 ms at a
-// quarter).
-int engine_subwarp(const asyrk_problem *p);
+// Sub-warp width of a slot in the multi-system engine: the single-system width
+// (tuned, else the default); in a batched solve, half of it (at least one lane).
+// A batch is judged by its total time, and a slot's share of the GPU leaves its
+// workers latency-bound, so twice the rows per warp in flight pay (256-system
+// batch: 92 ms against 97.5 ms at the full width, 94 ms at a quarter).  A served
+// solve is judged by its latency, and an engine step lasts as long as its
+// longest worker chain, which the narrower width lengthens (p50 12 ms against
+// 22 ms at Poisson 1000/s with the half width).
+int engine_subwarp(const asyrk_problem *p, bool batched);
 // x64 <-> x conversions over all slots (n_total entries laid out slot by slot)
 int launch_batch_convert(const double *x64, float *x, int64_t n_total, bool to_f32, cudaStream_t s);
 

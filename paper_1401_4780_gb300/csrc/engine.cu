@@ -627,11 +627,12 @@ int launch_batch_convert(const double *x64, float *x, int64_t n_total, bool to_f
     return ASYRK_OK;
 }
 
-int engine_subwarp(const asyrk_problem *p)
+int engine_subwarp(const asyrk_problem *p, bool batched)
 {
     bool tuned = false;
     int G = tuned_subwarp(p->dtype, p->max_len, p->nnz, p->m, &tuned);
     if (!tuned) G = choose_subwarp(p->max_len, p->nnz, p->m);
+    if (!batched) return G;
     return G > 1 ? G / 2 : 1;
 }
 

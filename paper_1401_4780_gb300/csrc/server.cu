@@ -249,7 +249,7 @@ static bool admit_locked(asyrk_server *sv, Request *r, int k)
     }
     SysDesc &D = sv->h[k];
     memset(&D, 0, sizeof D);
-    const int G = engine_subwarp(p);
+    const int G = engine_subwarp(p, false);
     const long long capw = tau_cap_estimate(p->m, p->n);
     const long long cw = (capw * G + 31) / 32;
     D.G = G;
