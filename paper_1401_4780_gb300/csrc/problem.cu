@@ -221,23 +221,41 @@ static void free_problem(asyrk_problem *p)
 // maximum; whether every row already starts at a multiple of 4.
 enum : unsigned { RP_FIRST = 1u, RP_EMPTY = 2u, RP_LONG = 4u, RP_MISALIGNED = 8u };
 
-__global__ void k_rowptr_pass(int64_t m, int64_t n, const int64_t *__restrict__ rp,
-                              int64_t *__restrict__ plen, unsigned long long *__restrict__ info)
+constexpr int RP_THREADS = 256;
+
+__global__ void __launch_bounds__(RP_THREADS) k_rowptr_pass(int64_t m, int64_t n,
+                                                           const int64_t *__restrict__ rp,
+                                                           int64_t *__restrict__ plen,
+                                                           unsigned long long *__restrict__ info)
 {
-    // info[0]: flags, info[1]: max row length, info[2]: first bad row
+    // info[0]: flags, info[1]: max row length, info[2]: first bad row.  Flags and
+    // the maximum are reduced over the block first: one atomic per block rather
+    // than one per row on a single address.
+    __shared__ unsigned s_len[RP_THREADS / 32], s_flag[RP_THREADS / 32];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const int64_t s = rp[i], len = rp[i + 1] - s;
-    unsigned f = 0;
-    if (i == 0 && s != 0) f |= RP_FIRST;
-    if (len <= 0) f |= RP_EMPTY;
-    if (len > n) f |= RP_LONG;
-    if (s & 3) f |= RP_MISALIGNED;
-    plen[i] = len > 0 ? ((len + 3) & ~(int64_t)3) : 0;
-    if (len > 0) atomicMax(&info[1], (unsigned long long)len);
-    if (f) {
-        atomicOr(&info[0], (unsigned long long)f);
+    unsigned f = 0, l32 = 0;
+    if (i < m) {
+        const int64_t s = rp[i], len = rp[i + 1] - s;
+        if (i == 0 && s != 0) f |= RP_FIRST;
+        if (len <= 0) f |= RP_EMPTY;
+        if (len > n) f |= RP_LONG;
+        if (s & 3) f |= RP_MISALIGNED;
+        plen[i] = len > 0 ? ((len + 3) & ~(int64_t)3) : 0;
+        l32 = len <= 0 ? 0u : len > 0xffffffffLL ? 0xffffffffu : (unsigned)len;
         if (f & (RP_FIRST | RP_EMPTY | RP_LONG)) atomicMin(&info[2], (unsigned long long)i);
+    }
+    l32 = __reduce_max_sync(0xffffffffu, l32);
+    f = __reduce_or_sync(0xffffffffu, f);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_len[w] = l32; s_flag[w] = f; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < RP_THREADS / 32; ++k) {
+            l32 = max(l32, s_len[k]);
+            f |= s_flag[k];
+        }
+        if (l32) atomicMax(&info[1], (unsigned long long)l32);
+        if (f) atomicOr(&info[0], (unsigned long long)f);
     }
 }
 
@@ -283,7 +301,7 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
     ASYRK_CKC(cudaMalloc((void **)&info_d, 3 * sizeof(unsigned long long)));
     ASYRK_CKC(cudaMemsetAsync(info_d, 0, 2 * sizeof(unsigned long long), s));
     ASYRK_CKC(cudaMemsetAsync(info_d + 2, 0xff, sizeof(unsigned long long), s));
-    k_rowptr_pass<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, n, rp_d, plen_d, info_d);
+    k_rowptr_pass<<<(unsigned)((m + RP_THREADS - 1) / RP_THREADS), RP_THREADS, 0, s>>>(m, n, rp_d, plen_d, info_d);
     ASYRK_CKC(cudaGetLastError());
     int st = exclusive_scan(plen_d, ps_d, m, scan_tmp, ps_d + m, s);
     if (st != ASYRK_OK) return fail(st);
