@@ -122,3 +122,28 @@ def test_adaptive_check_interval_stops_at_the_same_place_with_few_checks(samplin
     # ... after far fewer checks (one per check interval)
     assert fixed.project_launches == fixed.sweeps
     assert adaptive.project_launches < 0.25 * fixed.project_launches
+
+
+@pytest.mark.parametrize("row", range(6))
+def test_table2_shapes_epochs_within_the_papers_band(row):
+    """Each of Table 2's six shapes at full size (Section 5's generator, FP32,
+    shuffled sweeps as in the paper's implementation) reaches ||A^T(Ax-b)||^2 <=
+    1e-5 in an epoch count (iterations / n) within a factor 2 of the printed one."""
+    import torch
+    from golden import table2_asyrk
+    m, n, delta, _, epochs_paper = table2_asyrk()[row]
+    d = synth.make_system_torch(m, n, ("poisson", delta * n), 7000 + row, row_norms="unit",
+                                value_dtype="f32")
+    torch.cuda.synchronize()
+    with asyrk.Problem(m, n, d["row_ptr"], d["col"], d["val_store"], asyrk.F32, d["b"],
+                       seed=synth.solver_seed(7000 + row), device_ptrs=True) as p:
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        st, info = p.solve(x, tol=1e-5, max_sweeps=3000, device_ptrs=True, check_every=0,
+                           measure=asyrk.MEASURE_NORMAL_RESIDUAL, sampling=asyrk.SAMPLE_SHUFFLED)
+        assert st == asyrk.OK, info.as_dict()
+        assert p.normal_residual(x, x_on_device=True) <= 1e-5
+    epochs = info.projections / n
+    assert 0.5 * epochs_paper <= epochs <= 2.0 * epochs_paper, (epochs, epochs_paper)
+    del d
+    torch.cuda.empty_cache()
