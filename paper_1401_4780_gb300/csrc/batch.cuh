@@ -107,10 +107,10 @@ int tuned_subwarp(int dtype, int64_t max_len, int64_t nnz, int64_t m, bool *foun
 
 // Sub-warp width of a slot in the multi-system engine: the single-system width
 // (tuned, else the default); in a batched solve, half of it (at least one lane).
-// A batch is judged by its total time, and a slot's share of the GPU leaves its
+// What counts for a batch is its total time, and a slot's share of the GPU leaves its
 // workers latency-bound, so twice the rows per warp in flight pay (256-system
-// batch: 92 ms against 97.5 ms at the full width, 94 ms at a quarter).  A served
-// solve is judged by its latency, and an engine step lasts as long as its
+// batch: 92 ms against 97.5 ms at the full width, 94 ms at a quarter).  For a served
+// solve it is the latency, and an engine step lasts as long as its
 // longest worker chain, which the narrower width lengthens (p50 12 ms against
 // 22 ms at Poisson 1000/s with the half width).
 int engine_subwarp(const asyrk_problem *p, bool batched);
