@@ -654,12 +654,26 @@ def extras_batched(asyrk, synth, torch, graph=True):
                          "projections_per_s": r.projections_per_s, "trials": r.trials}
     xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for (_, n, _) in shapes]
     tols = [1e-6] * len(shapes)
-    with asyrk.Batch(probs, graph=graph) as b:
-        b.solve(xs, tols=tols, max_sweeps=400, x_trues=x_trues, device_ptrs=True)  # warm-up
-        for x in xs:
-            x.zero_()
-        torch.cuda.synchronize()
-        st, infos, bi = b.solve(xs, tols=tols, max_sweeps=400, x_trues=x_trues, device_ptrs=True)
+
+    def run(engine):
+        with asyrk.Batch(probs, graph=graph, engine=engine) as b:
+            b.solve(xs, tols=tols, max_sweeps=400, x_trues=x_trues, device_ptrs=True)  # warm-up
+            for x in xs:
+                x.zero_()
+            torch.cuda.synchronize()
+            return b.solve(xs, tols=tols, max_sweeps=400, x_trues=x_trues, device_ptrs=True)
+
+    # the global-iterate engine first, then the default (on-chip when every member fits)
+    st_g, infos_g, bi_g = run(asyrk.ENGINE_GLOBAL)
+    errs_g = [float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)) for x, xt in zip(xs, x_trues)]
+    global_engine = {"status": st_g, "converged": bi_g.converged, "device_ms": bi_g.device_ms,
+                     "wall_ms": 1e3 * bi_g.seconds, "iterations": bi_g.iterations,
+                     "projections_per_s": bi_g.projections / (bi_g.device_ms / 1e3),
+                     "max_rel_err_host": max(errs_g), "kernel_launches": bi_g.kernel_launches,
+                     "resident_warps": bi_g.resident_warps}
+    for x in xs:
+        x.zero_()
+    st, infos, bi = run(asyrk.ENGINE_AUTO)
     errs = [float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)) for x, xt in zip(xs, x_trues)]
     # the plain single-system FP32 kernel, one system after another, same tolerance
     t_plain, proj_plain, ok_plain = 0.0, 0, 0
@@ -679,6 +693,10 @@ def extras_batched(asyrk, synth, torch, graph=True):
            "systems": len(shapes), "sum_m": int(sum(m for m, _, _ in shapes)),
            "sum_nnz": int(sum(m * L for m, _, L in shapes)), "status": st,
            "converged": bi.converged, "iterations": bi.iterations, "graph_launch": bool(bi.graph),
+           "engine": {1: "global iterate (L2 atomics)",
+                      2: "on-chip: one thread-block cluster per system, x in distributed shared "
+                         "memory"}.get(bi.engine, bi.engine),
+           "workers_per_system_median": float(np.median([i.workers for i in infos])),
            "device_ms": bi.device_ms, "wall_ms": 1e3 * bi.seconds,
            "projections_per_s": bi.projections / (bi.device_ms / 1e3),
            "row_stream_gbs": alg_bytes / (bi.device_ms / 1e3) / 1e9,
@@ -689,7 +707,9 @@ def extras_batched(asyrk, synth, torch, graph=True):
            "resident_warps": bi.resident_warps, "autotuned_by_row_length_class": tuned,
            "plain_fp32_one_at_a_time": {"wall_ms": 1e3 * t_plain, "converged": ok_plain,
                                         "projections_per_s": proj_plain / t_plain},
-           "speedup_vs_one_at_a_time": t_plain / bi.seconds}
+           "speedup_vs_one_at_a_time": t_plain / bi.seconds,
+           "global_engine": global_engine,
+           "speedup_vs_global_engine": bi_g.device_ms / bi.device_ms}
     for p in probs:
         p.close()
     return out

@@ -276,23 +276,43 @@ typedef struct asyrk_tune_result {
 int asyrk_autotune(asyrk_problem *p, int64_t trial_projections, int force, asyrk_tune_result *res);
 
 /* ------------------------------------------------------------------------
- * Batched solves (not in the paper): many independent FP32/BF16 problems
- * advanced together by one persistent projection kernel.  Each iteration
- * splits the GPU's resident warps among the unfinished problems in proportion
- * to their stored entries, each capped by its own Cor. 2 worker estimate, and
- * runs one sweep of each; an FP64 check then retires the problems that met
- * their tolerance.  With graph >= 0 the whole loop is one CUDA graph launch
- * (a WHILE conditional node whose body is that iteration; the device stops
- * it), else a host loop.
+ * Batched solves (not in the paper): many independent FP32/BF16 problems.
+ * The global-iterate engine advances its members together by one persistent
+ * projection kernel: each iteration splits the GPU's resident warps among the
+ * unfinished problems in proportion to their stored entries, each capped by
+ * its own Cor. 2 worker estimate, and runs one sweep of each; an FP64 check
+ * then retires the problems that met their tolerance.  With graph >= 0 the
+ * whole loop is one CUDA graph launch (a WHILE conditional node whose body is
+ * that iteration; the device stops it), else a host loop.  The on-chip engine
+ * (asyrk_engine below) takes the members that fit a CTA's shared memory.
  * ------------------------------------------------------------------------ */
 typedef struct asyrk_batch asyrk_batch; /* opaque; owns per-problem iterates and tables */
 
+/* Which engine advances a batch's members.  ONCHIP (not in the paper): a
+ * member is solved by one CTA -- or a thread-block cluster of C <= cluster_max
+ * CTAs -- that keeps its FP32 iterate and row-claim bits in shared memory for
+ * the whole solve (gathers and atomic adds never leave the SM; only the row
+ * stream comes from HBM), checks its measure after every sweep on the device
+ * and writes x back at the end; such members run as independent nodes of one
+ * CUDA graph.  It needs the full-row update and ceil(n/C) + ceil(m/32)/C
+ * words per CTA within 200 KiB, and it gives a member at most the CTA's (or
+ * cluster's) threads.  GLOBAL: the iterate-in-HBM/L2 engine described above,
+ * which can give one member the whole GPU.  AUTO: the members that fit go
+ * on-chip, except the largest ones while the global engine, running at the
+ * same time on a second stream, would still finish first with them. */
+typedef enum { ASYRK_ENGINE_AUTO = 0, ASYRK_ENGINE_GLOBAL = 1, ASYRK_ENGINE_ONCHIP = 2 } asyrk_engine;
+
 typedef struct asyrk_batch_opts {
     void *stream;           /* cudaStream_t; NULL = legacy default stream          */
-    int32_t graph;          /* >= 0: one graph launch per solve (default); -1: host loop */
+    int32_t graph;          /* >= 0: one graph launch per solve (default); -1: host loop
+                               (ONCHIP: the members' launches one after another)   */
     int32_t row_exclusion;  /* as in asyrk_solve_opts                               */
     int32_t sampling;       /* asyrk_sampling of every member                       */
     int32_t update;         /* asyrk_update of every member                         */
+    int32_t engine;         /* asyrk_engine (0: AUTO)                               */
+    int32_t cluster_max;    /* ONCHIP: CTAs per cluster at most, 1, 2, 4 or 8 (0: 4) */
+    int32_t workers;        /* ONCHIP: workers per member at most (0: the Cor. 2
+                               estimate; 1: one worker, projections strictly in order) */
 } asyrk_batch_opts;
 
 typedef struct asyrk_batch_info {
@@ -305,6 +325,8 @@ typedef struct asyrk_batch_info {
     int64_t kernel_launches;  /* kernels run by the call (graph nodes included)    */
     int32_t resident_warps;   /* warps the engine splits among the problems        */
     int32_t graph;            /* 1: the loop ran as one graph launch               */
+    int32_t engine;           /* engines that ran: GLOBAL (1), ONCHIP (2), both (3) */
+    int32_t onchip_members;   /* members the on-chip engine solved                 */
 } asyrk_batch_info;
 
 /* Group `count` problems (FP32 or BF16 values, all on the current device, each

@@ -23,6 +23,7 @@ MODE_SEQUENTIAL, MODE_ASYNC, MODE_REFINE = 0, 1, 2
 MEASURE_AUTO, MEASURE_RESIDUAL, MEASURE_NORMAL_RESIDUAL = 0, 1, 2
 SAMPLE_WEIGHTED, SAMPLE_SHUFFLED = 0, 1
 UPDATE_ROW, UPDATE_SINGLE = 0, 1
+ENGINE_AUTO, ENGINE_GLOBAL, ENGINE_ONCHIP = 0, 1, 2
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
 
 
@@ -183,7 +184,8 @@ class TuneResult(ctypes.Structure):
 class BatchOpts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("graph", ctypes.c_int32),
                 ("row_exclusion", ctypes.c_int32), ("sampling", ctypes.c_int32),
-                ("update", ctypes.c_int32)]
+                ("update", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("cluster_max", ctypes.c_int32), ("workers", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -191,7 +193,8 @@ class BatchInfo(ctypes.Structure):
                 ("iterations", ctypes.c_int64), ("projections", ctypes.c_int64),
                 ("seconds", ctypes.c_double), ("device_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("resident_warps", ctypes.c_int32),
-                ("graph", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("onchip_members", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -356,11 +359,13 @@ def _ptr_array(items):
 
 
 def asyrk_batch_create(handles, stream=None, graph=True, row_exclusion=0,
-                       sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW):
+                       sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW, engine=0, cluster_max=0,
+                       workers=0):
     b = ctypes.c_void_p()
     hs = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
     o = BatchOpts(stream=_stream(stream), graph=0 if graph else -1, row_exclusion=row_exclusion,
-                  sampling=sampling, update=update)
+                  sampling=sampling, update=update, engine=engine, cluster_max=cluster_max,
+                  workers=workers)
     st = load().asyrk_batch_create(ctypes.byref(b), hs, len(handles), ctypes.byref(o))
     return st, b
 
@@ -582,10 +587,12 @@ class Batch:
     """Owns one asyrk_batch handle over a list of Problem objects."""
 
     def __init__(self, problems, stream=None, graph=True, row_exclusion=0,
-                 sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW):
+                 sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW, engine=0, cluster_max=0,
+                 workers=0):
         self.problems = list(problems)
         st, b = asyrk_batch_create([p.h for p in self.problems], stream=stream, graph=graph,
-                                   row_exclusion=row_exclusion, sampling=sampling, update=update)
+                                   row_exclusion=row_exclusion, sampling=sampling, update=update,
+                                   engine=engine, cluster_max=cluster_max, workers=workers)
         if st != OK:
             raise AsyrkError(st, "asyrk_batch_create")
         self.b = b

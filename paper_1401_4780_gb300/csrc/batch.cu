@@ -1,21 +1,31 @@
-// batch.cu -- asyrk_batch_*: many independent systems solved by one graph launch.
+// batch.cu -- asyrk_batch_*: many independent systems solved by graph launches.
 //
 // asyrk_batch_create fixes the member problems, picks each one's sub-warp
 // width (the autotuner's choice for its row length when tuned, else one
-// 4-entry chunk per lane) and its worker cap (the Cor. 2 estimate), lays out
-// the per-slot buffers and captures the whole solve as a CUDA graph whose only
-// top-level node is a WHILE conditional over one engine iteration (plan,
-// project, check, cond; see batch.cuh).  The loop stops on the device when no
-// slot is active or after the iteration bound, so asyrk_batch_solve is: copy
-// inputs, one measure launch, one graph launch, copy results.
+// 4-entry chunk per lane) and its worker cap (the Cor. 2 estimate), and splits
+// the members between two engines:
+//   * on-chip (cluster.cu): a member whose iterate fits a CTA's shared memory
+//     is solved start to finish by one CTA; these launches are the nodes of
+//     one CUDA graph;
+//   * global iterate (batch.cuh, engine.cu): the other members, advanced
+//     together by the multi-system engine; its whole loop is one CUDA graph
+//     whose only top-level node is a WHILE conditional over one engine
+//     iteration (plan, project, check, cond), stopped on the device when no
+//     slot is active or after the iteration bound.
+// The largest members that fit still go to the global engine while that
+// shortens the estimated batch time (plan_members).  asyrk_batch_solve: copy
+// inputs, launch both graphs on two streams at once, copy results.
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
+#include <numeric>
 #include <set>
 #include <vector>
 
 #include "batch.cuh"
+#include "cluster.cuh"
 
 struct asyrk_batch {
     int count = 0;
@@ -43,6 +53,17 @@ struct asyrk_batch {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     int64_t launches_per_iter = 4;
+    // the on-chip engine: members whose iterate fits a CTA's shared memory
+    std::vector<char> on;                // per member: 1 on-chip, 0 global-iterate engine
+    int n_on = 0, n_glob = 0;
+    std::vector<asyrk::ClusterShape> shapes;
+    std::vector<asyrk::ClusterJob> hj;   // host mirror of the job table
+    asyrk::ClusterJob *jobs = nullptr;
+    std::vector<int> order;              // on-chip members, longest estimated solve first
+    cudaGraph_t g_on = nullptr;
+    cudaGraphExec_t exec_on = nullptr;
+    cudaStream_t side = nullptr;         // the global engine's stream when both run
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 using namespace asyrk;
@@ -52,6 +73,11 @@ static void batch_free(asyrk_batch *b)
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->g) cudaGraphDestroy(b->g);
+    if (b->exec_on) cudaGraphExecDestroy(b->exec_on);
+    if (b->g_on) cudaGraphDestroy(b->g_on);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     cudaFree(b->d);
     cudaFree(b->x);
     cudaFree(b->x64);
@@ -60,6 +86,7 @@ static void batch_free(asyrk_batch *b)
     cudaFree(b->part);
     cudaFree(b->d_active);
     cudaFree(b->d_iter);
+    cudaFree(b->jobs);
     if (b->h_ints) cudaFreeHost(b->h_ints);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->ev[0]) cudaEventDestroy(b->ev[0]);
@@ -104,6 +131,119 @@ static int build_graph(asyrk_batch *b)
     return ASYRK_OK;
 }
 
+// The on-chip engine's graph: one kernel node per on-chip member, no
+// dependencies, the longest estimated solves placed first.
+static int build_onchip_graph(asyrk_batch *b)
+{
+    ASYRK_CK(cudaGraphCreate(&b->g_on, 0));
+    for (int k : b->order) {
+        int st = cluster_add_node(b->g_on, b->probs[k]->dtype, b->shapes[k], b->jobs, k);
+        if (st != ASYRK_OK) return st;
+    }
+    ASYRK_CK(cudaGraphInstantiate(&b->exec_on, b->g_on, 0));
+    return ASYRK_OK;
+}
+
+// Estimated time of one sweep of member k on its own CTA or cluster.
+static double onchip_sweep_seconds(const asyrk_batch *b, int k)
+{
+    const asyrk_problem *p = b->probs[k];
+    const ClusterShape &sh = b->shapes[k];
+    const int64_t chunks = (p->max_len + 4 * sh.G - 1) / (4 * sh.G);
+    const int64_t held = sh.G > 1 ? 2 : 1;  // chunks a lane keeps in registers
+    const double per = ONCHIP_SECONDS_PER_PROJECTION *
+                       (1.0 + ONCHIP_TAIL_CHUNK_FACTOR * (double)(chunks > held ? chunks - held : 0));
+    return (double)p->m * per / sh.workers;
+}
+
+// Estimated time of one sweep of member k in the global engine when it has
+// the GPU to itself: its Cor. 2 worker cap at the L2-bound projection time.
+static double global_sweep_seconds(const asyrk_batch *b, int k)
+{
+    const asyrk_problem *p = b->probs[k];
+    return (double)p->m * GLOBAL_SECONDS_PER_PROJECTION / (double)tau_cap_estimate(p->m, p->n);
+}
+
+// Which members the on-chip engine takes (b->on).  GLOBAL: none.  ONCHIP:
+// all, EINVAL when one does not fit.  AUTO: those that fit, less the ones
+// whose move to the global-iterate engine shortens the estimated batch time.
+// Both engines run at once; per sweep, the on-chip part lasts as long as its
+// longest member (or its thread-time over the GPU's threads, if longer), the
+// global part as long as its longest member or its projections at the global
+// rate, whichever is longer (constants measured, in cluster.cuh).
+static int plan_members(asyrk_batch *b, int engine, int cluster_max, int max_workers, int update)
+{
+    b->on.assign(b->count, 0);
+    if (engine == ASYRK_ENGINE_GLOBAL) return ASYRK_OK;
+    if (update != ASYRK_UPDATE_ROW) {
+        if (engine == ASYRK_ENGINE_ONCHIP)
+            return set_error(ASYRK_EINVAL, "the on-chip engine runs the full-row update only");
+        return ASYRK_OK;
+    }
+    b->shapes.assign(b->count, ClusterShape());
+    std::set<long long> prepared;
+    std::vector<int> cand;
+    for (int k = 0; k < b->count; ++k) {
+        asyrk_problem *p = b->probs[k];
+        int st = cluster_shape(p, engine_subwarp(p, true), cluster_max, max_workers, &b->shapes[k]);
+        if (st != ASYRK_OK) return st;
+        const ClusterShape &sh = b->shapes[k];
+        if (!sh.fits) {
+            if (engine == ASYRK_ENGINE_ONCHIP)
+                return set_error(ASYRK_EINVAL, "problem %d (m=%lld, n=%lld) does not fit the shared "
+                                 "memory of a cluster", k, (long long)p->m, (long long)p->n);
+            continue;
+        }
+        const long long key = ((long long)p->dtype * 64 + sh.G) * 2 + (sh.C > 1 ? 1 : 0);
+        if (prepared.insert(key).second && (st = cluster_prepare(p->dtype, sh.G, sh.C)) != ASYRK_OK)
+            return st;
+        if ((st = cluster_check_schedulable(p->dtype, sh)) != ASYRK_OK) {
+            if (engine == ASYRK_ENGINE_ONCHIP) return st;
+            continue;
+        }
+        cand.push_back(k);
+    }
+    size_t first = 0;
+    if (engine == ASYRK_ENGINE_AUTO && !cand.empty()) {
+        std::vector<char> is_cand(b->count, 0);
+        for (int k : cand) is_cand[k] = 1;
+        double g_long = 0.0, g_proj = 0.0;  // the global part: longest member, projections
+        for (int k = 0; k < b->count; ++k) {
+            if (is_cand[k]) continue;
+            g_long = std::max(g_long, global_sweep_seconds(b, k));
+            g_proj += (double)b->probs[k]->m;
+        }
+        std::stable_sort(cand.begin(), cand.end(), [&](int u, int v) {
+            return onchip_sweep_seconds(b, u) > onchip_sweep_seconds(b, v);
+        });
+        // thread-seconds per sweep of the on-chip members from position q on
+        std::vector<double> area(cand.size() + 1, 0.0);
+        for (size_t q = cand.size(); q-- > 0;)
+            area[q] = area[q + 1] + onchip_sweep_seconds(b, cand[q]) *
+                                        (double)b->shapes[cand[q]].threads * b->shapes[cand[q]].C;
+        const double gpu_threads = THREADS_PER_SM * b->probs[0]->sm_count;
+        auto on_time = [&](size_t q) {
+            return q < cand.size() ? std::max(onchip_sweep_seconds(b, cand[q]), area[q] / gpu_threads)
+                                   : 0.0;
+        };
+        auto glob_time = [&](double lng, double proj) {
+            return std::max(lng, proj / GLOBAL_PROJECTIONS_PER_SECOND);
+        };
+        while (first < cand.size()) {
+            const int k = cand[first];
+            const double now = std::max(on_time(first), glob_time(g_long, g_proj));
+            const double l2 = std::max(g_long, global_sweep_seconds(b, k));
+            const double p2 = g_proj + (double)b->probs[k]->m;
+            if (std::max(on_time(first + 1), glob_time(l2, p2)) >= now) break;
+            g_long = l2;
+            g_proj = p2;
+            ++first;
+        }
+    }
+    for (size_t q = first; q < cand.size(); ++q) b->on[cand[q]] = 1;
+    return ASYRK_OK;
+}
+
 extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *problems, int count,
                                   const asyrk_batch_opts *opts)
 {
@@ -118,6 +258,12 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
     if (o.sampling < ASYRK_SAMPLE_WEIGHTED || o.sampling > ASYRK_SAMPLE_SHUFFLED ||
         o.update < ASYRK_UPDATE_ROW || o.update > ASYRK_UPDATE_SINGLE)
         return set_error(ASYRK_EINVAL, "unknown sampling or update");
+    if (o.engine < ASYRK_ENGINE_AUTO || o.engine > ASYRK_ENGINE_ONCHIP)
+        return set_error(ASYRK_EINVAL, "unknown engine %d", (int)o.engine);
+    if (o.cluster_max != 0 && o.cluster_max != 1 && o.cluster_max != 2 && o.cluster_max != 4 &&
+        o.cluster_max != 8)
+        return set_error(ASYRK_EINVAL, "cluster_max must be 0, 1, 2, 4 or 8");
+    if (o.workers < 0) return set_error(ASYRK_EINVAL, "workers < 0");
     std::set<asyrk_problem *> seen;
     int dev = -1;
     ASYRK_CK(cudaGetDevice(&dev));
@@ -206,7 +352,50 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
         b->h[k].x64 = b->x64 + b->xoff[k];
         b->h[k].busy = b->busy + busy_off[k];
     }
-    if (b->graph && (st = build_graph(b)) != ASYRK_OK) return fail(st);
+    if ((st = plan_members(b, o.engine, o.cluster_max, o.workers, o.update)) != ASYRK_OK)
+        return fail(st);
+    for (int k = 0; k < count; ++k) (b->on[k] ? b->n_on : b->n_glob) += 1;
+    if (b->n_on > 0) {
+        for (int k = 0; k < count; ++k)
+            if (b->on[k]) b->order.push_back(k);
+        std::stable_sort(b->order.begin(), b->order.end(), [&](int u, int v) {
+            return onchip_sweep_seconds(b, u) > onchip_sweep_seconds(b, v);
+        });
+        b->hj.assign(count, ClusterJob());
+        for (int k : b->order) {
+            asyrk_problem *p = problems[k];
+            const ClusterShape &sh = b->shapes[k];
+            ClusterJob &J = b->hj[k];
+            memset(&J, 0, sizeof J);
+            J.rec = p->rec;
+            J.col = p->col;
+            J.val = p->val;
+            J.x64 = b->x64 + b->xoff[k];
+            J.x32 = b->x + b->xoff[k];
+            J.key = b->h[k].key;
+            J.m = (unsigned)p->m;
+            J.n = (unsigned)p->n;
+            J.uniform = p->uniform;
+            J.sampling = o.sampling;
+            J.shuf_h = b->h[k].shuf_h;
+            J.excl = b->excl ? 1 : 0;
+            J.workers = sh.workers;
+            J.lc = sh.lc;
+            J.nper = sh.nper;
+            J.nper_pad = sh.nper_pad;
+            J.bper = sh.bper;
+        }
+        e = cudaMalloc((void **)&b->jobs, count * sizeof(ClusterJob));
+        if (e == cudaSuccess && b->n_glob > 0)
+            e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess && b->n_glob > 0)
+            e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess && b->n_glob > 0)
+            e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "on-chip batch set-up", __FILE__, __LINE__));
+        if (b->graph && (st = build_onchip_graph(b)) != ASYRK_OK) return fail(st);
+    }
+    if (b->n_glob > 0 && b->graph && (st = build_graph(b)) != ASYRK_OK) return fail(st);
     *out = b;
     return ASYRK_OK;
 }
@@ -260,36 +449,80 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
             if (st != ASYRK_OK) return st;
         }
     }
+    // on-chip members sit out of the global engine's table; their jobs get the
+    // solve's parameters
+    for (int k = 0; k < b->count; ++k) {
+        if (!b->on[k]) continue;
+        SysDesc &D = b->h[k];
+        D.active = 0;
+        ClusterJob &J = b->hj[k];
+        J.gamma = D.gamma;
+        J.tol = D.tol;
+        J.max_sweeps = max_sweeps;
+        J.j0 = D.j;
+        J.xt = D.xt;
+        J.bnorm = b->probs[k]->bnorm;
+        J.meas = J.meas0 = -1.0;
+        J.sweeps = 0;
+        J.skipped = 0;
+        J.status = ASYRK_NOT_CONVERGED;
+    }
     int st = launch_batch_convert(b->x64, b->x, b->n_total, true, s);
     if (st != ASYRK_OK) return st;
     ASYRK_CK(cudaMemcpyAsync(b->d, b->h.data(), b->count * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
+    if (b->n_on > 0)
+        ASYRK_CK(cudaMemcpyAsync(b->jobs, b->hj.data(), b->count * sizeof(ClusterJob),
+                                 cudaMemcpyHostToDevice, s));
     const int max_iter = (int)(max_sweeps < 0x3ffffffe ? max_sweeps + 1 : 0x3fffffff);
+    b->h_ints[1] = 0;
     b->h_ints[2] = 0;
     b->h_ints[3] = max_iter;
     ASYRK_CK(cudaMemcpyAsync(b->d_iter, b->h_ints + 2, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
-    if ((st = launch_batch_measure(b->d, b->count, b->total_chunks, b->part, s)) != ASYRK_OK) return st;
-    int64_t launches = 3;  // convert, measure, and the final convert below
+    int64_t launches = 2;  // the two conversions
     int64_t iters = 0;
     ASYRK_CK(cudaEventRecord(b->ev[0], s));
-    if (b->graph) {
-        ASYRK_CK(cudaGraphLaunch(b->exec, s));
-        ASYRK_CK(cudaMemcpyAsync(b->h_ints + 1, b->d_iter, sizeof(int), cudaMemcpyDeviceToHost, s));
-        ASYRK_CK(cudaStreamSynchronize(s));
-        iters = b->h_ints[1];
-    } else {
-        for (int it = 0; it < max_iter; ++it) {
-            if ((st = launch_batch_iteration(b->d, b->count, b->total_chunks, b->part,
-                                             b->resident_warps, b->excl, b->d_active, b->d_iter,
-                                             false, 0ull, s)) != ASYRK_OK)
-                return st;
-            ASYRK_CK(cudaMemcpyAsync(b->h_ints, b->d_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-            ASYRK_CK(cudaStreamSynchronize(s));
-            ++iters;
-            if (b->h_ints[0] == 0) break;
+    // the global engine's members: on a second stream when the on-chip engine
+    // runs at the same time (graph form), else on the batch's stream
+    cudaStream_t gs = (b->n_on > 0 && b->n_glob > 0 && b->graph) ? b->side : s;
+    if (b->n_glob > 0) {
+        if (gs != s) {
+            ASYRK_CK(cudaEventRecord(b->ev_fork, s));
+            ASYRK_CK(cudaStreamWaitEvent(gs, b->ev_fork, 0));
         }
+        if ((st = launch_batch_measure(b->d, b->count, b->total_chunks, b->part, gs)) != ASYRK_OK)
+            return st;
+        launches += 1;
+        if (b->graph) {
+            ASYRK_CK(cudaGraphLaunch(b->exec, gs));
+            ASYRK_CK(cudaMemcpyAsync(b->h_ints + 1, b->d_iter, sizeof(int), cudaMemcpyDeviceToHost, gs));
+        } else {
+            for (int it = 0; it < max_iter; ++it) {
+                if ((st = launch_batch_iteration(b->d, b->count, b->total_chunks, b->part,
+                                                 b->resident_warps, b->excl, b->d_active,
+                                                 b->d_iter, false, 0ull, gs)) != ASYRK_OK)
+                    return st;
+                ASYRK_CK(cudaMemcpyAsync(b->h_ints, b->d_active, sizeof(int), cudaMemcpyDeviceToHost, gs));
+                ASYRK_CK(cudaStreamSynchronize(gs));
+                ++b->h_ints[1];
+                if (b->h_ints[0] == 0) break;
+            }
+        }
+        if (gs != s) ASYRK_CK(cudaEventRecord(b->ev_join, gs));
     }
+    if (b->n_on > 0) {
+        if (b->graph) {
+            ASYRK_CK(cudaGraphLaunch(b->exec_on, s));
+        } else {
+            for (int k : b->order)
+                if ((st = cluster_launch(b->probs[k]->dtype, b->shapes[k], b->jobs, k, s)) != ASYRK_OK)
+                    return st;
+        }
+        launches += b->n_on;
+        ASYRK_CK(cudaMemcpyAsync(b->hj.data(), b->jobs, b->count * sizeof(ClusterJob),
+                                 cudaMemcpyDeviceToHost, s));
+    }
+    if (b->n_glob > 0 && gs != s) ASYRK_CK(cudaStreamWaitEvent(s, b->ev_join, 0));
     ASYRK_CK(cudaEventRecord(b->ev[1], s));
-    launches += 4 * iters;
     // results: x back to FP64, the final FP64 residual, the table
     if ((st = launch_batch_convert(b->x64, b->x, b->n_total, false, s)) != ASYRK_OK) return st;
     if ((st = launch_batch_residual(b->d, b->count, b->total_chunks, b->part, s)) != ASYRK_OK) return st;
@@ -300,6 +533,22 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
         ASYRK_CK(cudaMemcpyAsync(xs[k], b->x64 + b->xoff[k], b->probs[k]->n * sizeof(double),
                                  out_kind, s));
     ASYRK_CK(cudaStreamSynchronize(s));
+    if (b->n_glob > 0) {
+        iters = b->h_ints[1];
+        launches += 4 * iters;
+    }
+    for (int k = 0; k < b->count; ++k) {  // the on-chip members' outcomes
+        if (!b->on[k]) continue;
+        const ClusterJob &J = b->hj[k];
+        SysDesc &D = b->h[k];
+        D.sweeps = J.sweeps;
+        D.status = J.status;
+        D.meas = J.meas;
+        D.meas0 = J.meas0;
+        D.j = J.j0 + (unsigned long long)J.sweeps * (unsigned long long)J.m;
+        D.skipped = J.skipped;
+        if (J.sweeps > iters) iters = J.sweeps;
+    }
     float ms = 0.f;
     ASYRK_CK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
     const double secs =
@@ -318,7 +567,7 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
             asyrk_solve_info &I = infos[k];
             memset(&I, 0, sizeof I);
             I.status = D.status;
-            I.workers = D.first_nwarps * (32 / D.G);
+            I.workers = b->on[k] ? b->shapes[k].workers : D.first_nwarps * (32 / D.G);
             I.subwarp = D.G;
             I.sweeps = D.sweeps;
             I.projections = proj;
@@ -339,6 +588,8 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
         binfo->kernel_launches = launches;
         binfo->resident_warps = b->resident_warps;
         binfo->graph = b->graph ? 1 : 0;
+        binfo->engine = (b->n_glob > 0 ? ASYRK_ENGINE_GLOBAL : 0) | (b->n_on > 0 ? ASYRK_ENGINE_ONCHIP : 0);
+        binfo->onchip_members = b->n_on;
     }
     return worst;
 }

@@ -49,9 +49,9 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(asyrk.SolveOpts) == 80
     assert ctypes.sizeof(asyrk.SolveInfo) == 96
     assert ctypes.sizeof(asyrk.ProblemStats) == 80
-    assert ctypes.sizeof(asyrk.BatchOpts) == 24
+    assert ctypes.sizeof(asyrk.BatchOpts) == 40
     assert ctypes.sizeof(asyrk.LsqOpts) == 40
-    assert ctypes.sizeof(asyrk.BatchInfo) == 56
+    assert ctypes.sizeof(asyrk.BatchInfo) == 64
     assert ctypes.sizeof(asyrk.TuneResult) == 24
     assert ctypes.sizeof(asyrk.ServerOpts) == 32
     assert ctypes.sizeof(asyrk.ServerStats) == 88

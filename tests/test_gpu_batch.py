@@ -5,8 +5,9 @@
     within 1.5x the oracle's median sweep count for that system;
   * each system's result is the same alone (asyrk_solve) and in the mix, within
     the tolerance: both are within 1e-6 of x*;
-  * the graph launch and the host loop agree; the residual measure works
-    without x*; the sweep budget gives NOT_CONVERGED; bad batches are rejected;
+  * the graph launch and the host loop agree, with the global-iterate engine and
+    with the on-chip one; the residual measure works without x*; the sweep
+    budget gives NOT_CONVERGED; bad batches are rejected;
   * the autotuner returns a shape the solve then uses.
 """
 import numpy as np
@@ -40,16 +41,18 @@ def _err(x, s):
     return np.linalg.norm(x - s.x_true) / np.linalg.norm(s.x_true)
 
 
+@pytest.mark.parametrize("engine", [asyrk.ENGINE_GLOBAL, asyrk.ENGINE_ONCHIP])
 @pytest.mark.parametrize("graph", [True, False])
-def test_batch_reaches_tolerance_within_oracle_sweeps(graph):
+def test_batch_reaches_tolerance_within_oracle_sweeps(graph, engine):
     systems = _systems()
     probs = [asyrk.Problem.from_system(s) for s in systems]
-    with asyrk.Batch(probs, graph=graph) as b:
+    with asyrk.Batch(probs, graph=graph, engine=engine) as b:
         xs = [np.zeros(s.n) for s in systems]
         st, infos, bi = b.solve(xs, tols=[1e-6] * len(systems), max_sweeps=400,
                                 x_trues=[s.x_true for s in systems])
         assert st == asyrk.OK, [i.status for i in infos]
         assert bi.converged == len(systems) and bi.graph == (1 if graph else 0)
+        assert bi.engine == engine
         assert bi.iterations == max(i.sweeps for i in infos)
     for s, x, info in zip(systems, xs, infos):
         if s.value_dtype == "bf16":  # no tuned shape for these: the engine halves the default
