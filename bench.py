@@ -800,7 +800,8 @@ def extras_served(asyrk, synth, torch, seconds, rate):
            "per_class": {c: {"n": len(v), "p50_ms": 1e3 * float(np.percentile(v, 50)),
                              "p99_ms": 1e3 * float(np.percentile(v, 99))}
                          for c, v in sorted(lat.items())},
-           "engine_steps": stats["iterations"], "max_in_flight": stats["max_active"]}
+           "engine_steps": stats["iterations"], "max_in_flight": stats["max_active"],
+           "solved_on_chip": stats["onchip_completed"]}
     # the plain single-system FP32 kernel, one request at a time, at 1e-6
     times = {}
     for cls, count in (("small_f32", 16), ("large_f32", 2)):

@@ -373,6 +373,8 @@ typedef struct asyrk_server_opts {
     int32_t row_exclusion;     /* as in asyrk_solve_opts                             */
     double inner_tol;          /* REFINE inner target (0: 1e-3)                      */
     int64_t max_inner_sweeps;  /* REFINE inner sweeps per outer step at most (0: 60) */
+    int32_t onchip;            /* >= 0: requests whose problem fits a CTA's shared
+                                  memory are solved on-chip (default); -1: never     */
 } asyrk_server_opts;
 
 typedef struct asyrk_server_stats {
@@ -386,6 +388,7 @@ typedef struct asyrk_server_stats {
     int32_t max_active;        /* most requests in flight at once so far             */
     int32_t fatal;             /* first hard error of the engine, or OK              */
     int32_t reserved;
+    int64_t onchip_completed;  /* requests solved on-chip so far                     */
 } asyrk_server_stats;
 
 /* Start a server on the current device.  Errors: EINVAL, ENOMEM, ECUDA. */

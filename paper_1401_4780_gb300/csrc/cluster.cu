@@ -178,17 +178,19 @@ __device__ __forceinline__ double entry_f64(const bf16_t *v, long long k)
     return (double)__uint_as_float(((unsigned)v[k].bits) << 16);
 }
 
-// The FP64 measure of the cluster's current x: (||x - x*||^2, ||x*||^2) with
-// x*, else (||b - A x||^2, ||b||^2) with b at FP32 as the row records hold it.
+// The FP64 measure of the cluster's current x: (||x - x*||^2, ||x*||^2) when
+// err_form, else (||b - A x||^2, ||b||^2) with b at FP32 -- the row records'
+// b, or bvec (a refinement's right-hand side) when given.
 template <typename VT, bool DS>
 __device__ __forceinline__ void cluster_measure(const ClusterJob &J, const Slices<DS> &X,
                                                 const float *xs, unsigned rank, int C,
-                                                double *wsum, double *cta_part, double *tot,
-                                                double &t0, double &t1)
+                                                bool err_form, const float *bvec, double *wsum,
+                                                double *cta_part, double *tot, double &t0,
+                                                double &t1)
 {
     double v0 = 0.0, v1 = 0.0;
     const int T = (int)blockDim.x;
-    if (J.xt) {
+    if (err_form) {
         const int nper = J.nper;
         for (int o = threadIdx.x; o < nper; o += T) {
             const long long t = ((long long)o << J.lc) + rank;
@@ -207,7 +209,7 @@ __device__ __forceinline__ void cluster_measure(const ClusterJob &J, const Slice
             for (unsigned q = 0; q < r.len; ++q)
                 acc += entry_f64(val, r.start + q) *
                        (double)sh_ld<DS>(X.at((unsigned)J.col[r.start + q]));
-            const double bi = (double)r.b;
+            const double bi = bvec ? (double)__ldcg(bvec + i) : (double)r.b;
             const double ri = bi - acc;
             v0 += ri * ri;
             v1 += bi * bi;
@@ -216,8 +218,57 @@ __device__ __forceinline__ void cluster_measure(const ClusterJob &J, const Slice
     cluster_sum2<DS>(v0, v1, wsum, cta_part, tot, C, t0, t1);
 }
 
+// The outer step of mixed-precision refinement: x64 += d and d = 0 over this
+// CTA's entries; then, with every CTA's update in place, r = b - A x64 in FP64
+// over the cluster's rows, stored at FP32 in r32 (the next inner solve's
+// right-hand side).  Returns (||r||^2, ||x64 - x*||^2) (the latter 0 without x*).
+template <typename VT, bool DS>
+__device__ __forceinline__ void cluster_outer(const ClusterJob &J, float *xs, unsigned rank, int C,
+                                              double *wsum, double *cta_part, double *tot,
+                                              double &t0, double &t1)
+{
+    const int T = (int)blockDim.x;
+    for (int o = threadIdx.x; o < J.nper; o += T) {
+        const long long t = ((long long)o << J.lc) + rank;
+        if (t < J.n) J.x64[t] = __ldcg(J.x64 + t) + (double)xs[o];
+        xs[o] = 0.f;
+    }
+    cl_sync<DS>();  // x64 complete
+    double v0 = 0.0, v1 = 0.0;
+    const VT *val = static_cast<const VT *>(J.val);
+    for (long long i = (long long)rank * T + threadIdx.x; i < J.m; i += (long long)C * T) {
+        const RowRec r = load_rec(J.rec + i);
+        double acc = 0.0;
+        for (unsigned q = 0; q < r.len; ++q)
+            acc += entry_f64(val, r.start + q) * __ldcg(J.x64 + J.col[r.start + q]);
+        const double ri = J.b64[i] - acc;
+        J.r32[i] = (float)ri;
+        v0 += ri * ri;
+    }
+    if (J.xt) {
+        for (int o = threadIdx.x; o < J.nper; o += T) {
+            const long long t = ((long long)o << J.lc) + rank;
+            if (t < J.n) {
+                const double e = __ldcg(J.x64 + t) - J.xt[t];
+                v1 += e * e;
+            }
+        }
+    }
+    cluster_sum2<DS>(v0, v1, wsum, cta_part, tot, C, t0, t1);
+}
+
+// A solve's progress, kept in shared memory (thread 0 of each CTA writes it).
+struct SolveState {
+    double meas, meas0;  // last and first measure
+    double ref_in;       // refinement: ||r|| of the current inner solve
+    double res2;         // refinement: ||b - A x64||^2 of the last outer step
+    long long sweeps, inner_sweeps;
+    int status, outer_steps;
+    int done, outer_next;
+};
+
 // First half of the row draw of projection j (the global kernels' draw_row):
-// the Philox words at counter (j_lo, j_hi, 0, 0), the bucket floor(u0 m / 2^32)
+// the Philox words at counter (j_lo, j_hi, stream, 0), the bucket floor(u0 m / 2^32)
 // and its record; `coin` = u1 decides the alias later.  Shuffled sweeps: the
 // row pi_k(j mod m) and its record, no alias.
 __device__ __forceinline__ void prefetch_draw(unsigned long long j, const ClusterJob &J,
@@ -225,10 +276,11 @@ __device__ __forceinline__ void prefetch_draw(unsigned long long j, const Cluste
                                               unsigned &coin, RowRec &r)
 {
     if (J.sampling == 1) {
-        i = shuffled_position(j, m, 0u, J.key, J.shuf_h);
+        i = shuffled_position(j, m, J.stream_id, J.key, J.shuf_h);
         coin = 0u;
     } else {
-        const uint4 u = philox4x32_10(make_uint4((unsigned)j, (unsigned)(j >> 32), 0u, 0u), J.key);
+        const uint4 u = philox4x32_10(make_uint4((unsigned)j, (unsigned)(j >> 32), J.stream_id, 0u),
+                                      J.key);
         i = __umulhi(u.x, m);
         coin = u.y;
     }
@@ -244,6 +296,7 @@ __global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1) k_cluster_solve(Cluste
     __shared__ double tot[2];
     __shared__ unsigned long long cta_skipped;
     __shared__ ClusterJob sj;  // the job's fields, read from shared memory in the loops
+    __shared__ SolveState ss;
 
     if (threadIdx.x == 0) sj = jobs[k];
     __syncthreads();
@@ -256,29 +309,47 @@ __global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1) k_cluster_solve(Cluste
     const Slices<DS> X{smem_addr(xs), (unsigned)(C - 1), lc};
     const Slices<DS> B{smem_addr(bs), (unsigned)(C - 1), lc};
 
-    // 1. this CTA's slice of x from the FP64 iterate, claim bits cleared
+    // 1. this CTA's slice of the shared iterate -- x0 from the FP64 iterate, or
+    // for refinement the correction d = 0 -- and the claim bits cleared
+    const bool refine = J.refine != 0;
     for (int o = threadIdx.x; o < J.nper; o += T) {
         const long long t = ((long long)o << lc) + rank;
-        xs[o] = t < J.n ? (float)J.x64[t] : 0.f;
+        xs[o] = (t < J.n && !refine) ? (float)J.x64[t] : 0.f;
     }
     for (int o = threadIdx.x; o < J.bper; o += T) bs[o] = 0u;
     if (threadIdx.x == 0) cta_skipped = 0ull;
     cl_sync<DS>();  // all slices initialised (and, in a cluster, every CTA running)
 
-    // 2. the first measure
+    // 2. the first measure: ||x0 - x*|| / ||x*|| (or the residual); with
+    // refinement only ||x*|| (the outer measure's reference), the outer step
+    // measures the rest.  The solve's state lives in shared memory: thread 0
+    // of each CTA takes the decisions (every CTA from the same sums), every
+    // thread reads them after the next barrier.
     double t0, t1;
-    cluster_measure<VT, DS>(J, X, xs, rank, C, wsum, cta_part, tot, t0, t1);
+    cluster_measure<VT, DS>(J, X, xs, rank, C, J.xt != nullptr, nullptr, wsum, cta_part, tot, t0, t1);
     const double ref = J.xt ? (sqrt(t1) > 0.0 ? sqrt(t1) : 1.0) : (J.bnorm > 0.0 ? J.bnorm : 1.0);
-    double meas = sqrt(t0) / ref;
-    const double meas0 = meas;
-    int status = ASYRK_NOT_CONVERGED;
-    bool done = false;
-    if (meas <= J.tol) {
-        status = ASYRK_OK;
-        done = true;
-    } else if (J.max_sweeps <= 0) {
-        done = true;
+    if (threadIdx.x == 0) {
+        ss.meas = ss.meas0 = -1.0;
+        ss.ref_in = 1.0;
+        ss.res2 = 0.0;
+        ss.status = ASYRK_NOT_CONVERGED;
+        ss.outer_steps = 0;
+        ss.inner_sweeps = 0;
+        ss.sweeps = 0;
+        ss.done = 0;
+        ss.outer_next = refine ? 1 : 0;
+        if (!refine) {
+            ss.meas = ss.meas0 = sqrt(t0) / ref;
+            if (ss.meas <= J.tol) {
+                ss.status = ASYRK_OK;
+                ss.done = 1;
+            } else if (J.max_sweeps <= 0) {
+                ss.done = 1;
+            }
+        }
     }
+    __syncthreads();
+    const float *bvec = refine ? J.r32 : nullptr;
 
     // worker layout: cluster thread id -> worker (G lanes of one warp)
     const int lane = threadIdx.x & 31;
@@ -294,10 +365,38 @@ __global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1) k_cluster_solve(Cluste
     const bool excl = J.excl != 0;
     const bool seq = W == 1;
     unsigned long long skipped = 0;
-    long long sweeps = 0;
 
-    // 3. sweeps until the measure meets the tolerance (or diverges, or the budget ends)
-    while (!done) {
+    // 3. sweeps until the measure meets the tolerance (or diverges, or the budget
+    // ends); with refinement, outer steps r = b - A x64, x64 += d between inner
+    // solves of A d = r (the multi-system engine's refinement, in one CTA)
+    for (;;) {
+        if (ss.done) break;
+        if (ss.outer_next) {
+            cluster_outer<VT, DS>(J, xs, rank, C, wsum, cta_part, tot, t0, t1);
+            if (threadIdx.x == 0) {
+                const double rnorm = sqrt(t0);
+                const double meas = J.xt ? sqrt(t1) / ref : rnorm / ref;
+                ss.meas = meas;
+                if (ss.meas0 < 0.0) ss.meas0 = meas;
+                ss.outer_steps += 1;
+                ss.res2 = t0;
+                if (!isfinite(meas) || meas > 1e30 * (ss.meas0 > 0.0 ? ss.meas0 : 1.0)) {
+                    ss.status = ASYRK_DIVERGED;
+                    ss.done = 1;
+                } else if (meas <= J.tol || rnorm == 0.0) {
+                    ss.status = ASYRK_OK;
+                    ss.done = 1;
+                } else if (ss.sweeps >= J.max_sweeps) {
+                    ss.done = 1;
+                }
+                ss.outer_next = 0;
+                ss.ref_in = rnorm;
+                ss.inner_sweeps = 0;
+            }
+            cl_sync<DS>();  // r32 complete before the inner solve reads it; decisions visible
+            continue;
+        }
+        const long long sweeps = ss.sweeps;
         const unsigned long long jbase = J.j0 + (unsigned long long)sweeps * m;
         if (warp_first < W) {
             // The draw is split in two so that the record load of a worker's next
@@ -321,7 +420,7 @@ __global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1) k_cluster_solve(Cluste
                 }
                 const long long start = act ? r.start : 0;
                 int len = act ? (int)r.len : 0;
-                const float b = r.b, scale = r.inv;
+                const float b = (bvec && act) ? __ldcg(bvec + i) : r.b, scale = r.inv;
                 nact = worker && t + (unsigned long long)W < m;
                 if (nact) prefetch_draw(jbase + t + W, J, rec, m, ni, ncoin, nr);
                 // a lane's first two chunks of 4 entries (rows up to 8G entries) stay
@@ -420,23 +519,40 @@ __global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1) k_cluster_solve(Cluste
             }
         }
         cl_sync<DS>();  // the sweep's updates are all applied
-        ++sweeps;
-        cluster_measure<VT, DS>(J, X, xs, rank, C, wsum, cta_part, tot, t0, t1);
-        meas = sqrt(t0) / ref;
-        if (!isfinite(meas) || meas > 1e30 * (meas0 > 0.0 ? meas0 : 1.0)) {
-            status = ASYRK_DIVERGED;
-            done = true;
-        } else if (meas <= J.tol) {
-            status = ASYRK_OK;
-            done = true;
-        } else if (sweeps >= J.max_sweeps) {
-            done = true;
+        cluster_measure<VT, DS>(J, X, xs, rank, C, J.xt != nullptr && !refine, bvec, wsum,
+                                cta_part, tot, t0, t1);
+        if (threadIdx.x == 0) {
+            ss.sweeps = sweeps + 1;
+            if (refine) {  // inner solve: ||r - A d|| / ||r||
+                ss.inner_sweeps += 1;
+                const double mi = sqrt(t0) / ss.ref_in;
+                if (!isfinite(mi)) {
+                    ss.status = ASYRK_DIVERGED;
+                    ss.done = 1;
+                } else if (mi <= J.inner_tol || ss.inner_sweeps >= J.max_inner ||
+                           ss.sweeps >= J.max_sweeps) {
+                    ss.outer_next = 1;
+                }
+            } else {
+                const double meas = sqrt(t0) / ref;
+                ss.meas = meas;
+                if (!isfinite(meas) || meas > 1e30 * (ss.meas0 > 0.0 ? ss.meas0 : 1.0)) {
+                    ss.status = ASYRK_DIVERGED;
+                    ss.done = 1;
+                } else if (meas <= J.tol) {
+                    ss.status = ASYRK_OK;
+                    ss.done = 1;
+                } else if (ss.sweeps >= J.max_sweeps) {
+                    ss.done = 1;
+                }
+            }
         }
-        cl_sync<DS>();  // no CTA starts the next sweep while another still measures
+        cl_sync<DS>();  // decisions visible; no CTA starts the next sweep while another measures
     }
 
-    // 4. results: x to the FP32 iterate in HBM, counters
-    for (int o = threadIdx.x; o < J.nper; o += T) {
+    // 4. results: x to the FP32 iterate in HBM (refinement: x64 holds the
+    // iterate, the last outer step folded d into it), counters
+    for (int o = threadIdx.x; o < J.nper && !refine; o += T) {
         const long long t = ((long long)o << lc) + rank;
         if (t < J.n) J.x32[t] = xs[o];
     }
@@ -446,10 +562,12 @@ __global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1) k_cluster_solve(Cluste
     if (threadIdx.x == 0) {
         if (cta_skipped) atomicAdd(&Jw.skipped, cta_skipped);
         if (rank == 0) {
-            Jw.meas = meas;
-            Jw.meas0 = meas0;
-            Jw.sweeps = sweeps;
-            Jw.status = status;
+            Jw.meas = ss.meas;
+            Jw.meas0 = ss.meas0;
+            Jw.sweeps = ss.sweeps;
+            Jw.status = ss.status;
+            Jw.outer_steps = ss.outer_steps;
+            Jw.res2 = ss.res2;
         }
     }
     cl_sync<DS>();  // no CTA leaves while another may still read its shared memory

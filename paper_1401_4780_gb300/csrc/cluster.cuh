@@ -14,6 +14,7 @@ constexpr int CLUSTER_MAX_SIZE = 8;                // CTAs per cluster (portable
 // when its gathers and updates go to other CTAs of a cluster of 2-8.
 constexpr int CLUSTER_DEFAULT_MAX = 1;
 constexpr size_t CLUSTER_SMEM_BYTES = 200 * 1024;  // dynamic shared memory per CTA, at most
+constexpr int SERVER_ONCHIP_SLOTS = 64;            // on-chip requests a server runs at once
 // Cost model of a hybrid batch (measured on a GB300): the time one worker
 // takes per projection with the iterate in its CTA's shared memory (2.0 us
 // on a system whose rows stay in L2, 2.6 us on the largest members of the
@@ -30,17 +31,21 @@ constexpr double GLOBAL_SECONDS_PER_PROJECTION = 4.5e-6;
 constexpr double GLOBAL_PROJECTIONS_PER_SECOND = 1.7e9;
 constexpr double THREADS_PER_SM = 2048.0;
 
-// One member of a batch, read by its cluster; the host rewrites the per-solve
-// fields before each launch and reads the results after it.
+// One solve, read by its cluster (a batch member or a served request); the
+// host writes the per-solve fields before the launch and reads the results
+// after it.
 struct ClusterJob {
     const RowRec *rec;
     const int32_t *col;
     const void *val;
-    const double *x64; // in: x0 (FP64)
-    float *x32;        // out: x (FP32)
+    double *x64;       // in: x0 (FP64); refinement: the FP64 iterate, in and out
+    float *x32;        // out: x (FP32; plain solves)
     const double *xt;  // x* in FP64, or nullptr: measure ||b - A x|| / ||b||
+    const double *b64; // FP64 b (refinement's outer residual)
+    float *r32;        // refinement: workspace of m floats, r = b - A x64 at FP32
     uint2 key;
     unsigned m, n;
+    unsigned stream_id;  // Philox stream of the row sequence (a served request's ticket)
     int uniform;
     int sampling;      // 0: weighted i.i.d. draws, 1: shuffled sweeps
     int shuf_h;
@@ -51,6 +56,10 @@ struct ClusterJob {
     int nper_pad;      // nper rounded up to 4 (the claim words follow)
     int bper;          // claim words per CTA: ceil(ceil(m / 32) / C)
     float gamma;
+    int refine;        // 1: FP64 iterate x64 refined by FP32 inner solves (d on chip)
+    int pad0;
+    long long max_inner;  // refinement: inner sweeps per outer step at most
+    double inner_tol;     // refinement: inner target ||r - A d|| / ||r||
     // per solve
     unsigned long long j0;  // first projection of the row sequence
     long long max_sweeps;
@@ -61,7 +70,8 @@ struct ClusterJob {
     long long sweeps;
     unsigned long long skipped;
     int status;
-    int pad;
+    int outer_steps;   // refinement: outer steps taken
+    double res2;       // refinement: ||b - A x64||^2 of the last outer step
 };
 
 struct ClusterShape {

@@ -13,12 +13,18 @@
 //            kernel launch;
 //   harvest  finished slots copy their x back, free their memory and wake
 //            the request's waiter; the next admission can take the slot.
-// Every slot has its own Philox stream (the ticket), so one problem can serve
-// several requests at once.  The device never waits on the host: every wait
-// is host-side and has a time limit.
+// A request whose problem fits a CTA's shared memory (cluster.cu) skips the
+// shared engine step: it takes an on-chip slot, its whole solve (plain or
+// refined) is one CTA launch on the slot's own stream, and the engine thread
+// harvests it when the launch's event has completed; such requests may pass
+// queued requests that wait for memory or for a slot of the shared step.
+// Every request has its own Philox stream (the ticket), so one problem can
+// serve several requests at once.  The device never waits on the host: every
+// wait is host-side and has a time limit.
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -29,6 +35,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "cluster.cuh"
 
 namespace asyrk {
 
@@ -127,6 +134,8 @@ struct Request {
     bool done = false, cancelled = false;
     int slot = -1;
     size_t slot_bytes = 0;
+    bool onchip = false;   // solved by one CTA (ocshape) instead of the shared engine step
+    ClusterShape ocshape;
     asyrk_solve_info info;
 };
 
@@ -169,14 +178,30 @@ struct asyrk_server {
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request *> queue;
+    std::deque<Request *> queue;      // requests for the shared engine step
+    std::deque<Request *> oc_queue;   // requests solved on-chip
     std::unordered_map<uint64_t, Request *> reqs;
     uint64_t next_ticket = 1;
     bool stop = false;
     int fatal = ASYRK_OK;
     std::thread th;
+    std::thread oc_th;                // admits and harvests the on-chip requests
+    std::condition_variable cv_oc;
 
     int64_t submitted = 0, completed = 0, iterations = 0, launches = 0, max_active = 0;
+
+    // on-chip slots: one CTA launch per request, each slot with its own stream
+    bool onchip = true;
+    int oc_slots = 0;
+    std::vector<Request *> oc_req;
+    std::vector<SlotMem> oc_mem;
+    std::vector<ClusterJob> oc_hj;
+    ClusterJob *oc_jobs = nullptr;
+    std::vector<cudaStream_t> oc_stream;
+    std::vector<cudaEvent_t> oc_ev;
+    std::vector<float> oc_x32;          // staging of a plain solve's FP32 x
+    std::vector<long long> oc_prepared;  // (dtype, G) kernels given their shared memory
+    int64_t oc_completed = 0;
 };
 
 static size_t request_bytes(const asyrk_problem *p, bool has_xt, int mode)
@@ -315,7 +340,158 @@ static void release_slot_locked(asyrk_server *sv, int k)
     r->slot = -1;
 }
 
-static void fail_all_locked(asyrk_server *sv, int status)
+// admit request r into on-chip slot k and launch its solve (engine thread,
+// sv->mu held); false: no memory now
+static bool admit_onchip_locked(asyrk_server *sv, Request *r, int k)
+{
+    asyrk_problem *p = r->p;
+    const bool has_xt = !r->xt.empty();
+    const bool refine = r->mode == ASYRK_MODE_REFINE;
+    const size_t need = r->slot_bytes + (sv->problem_refs.count(p) ? 0 : (size_t)p->dev_bytes);
+    if (sv->used + need > sv->budget) return false;
+    SlotMem M;
+    M.bx = (size_t)p->n * 4;
+    M.bx64 = (size_t)p->n * 8;
+    M.bxt = has_xt ? (size_t)p->n * 8 : 0;
+    M.br32 = refine ? (size_t)p->m * 4 : 0;
+    M.x = (float *)sv->arena->alloc(M.bx);
+    M.x64 = (double *)sv->arena->alloc(M.bx64);
+    if (has_xt) M.xt = (double *)sv->arena->alloc(M.bxt);
+    if (refine) M.r32 = (float *)sv->arena->alloc(M.br32);
+    sv->oc_mem[k] = M;
+    if (!M.x || !M.x64 || (has_xt && !M.xt) || (refine && !M.r32)) {
+        SlotMem &F = sv->oc_mem[k];
+        sv->arena->release(F.x, F.bx);
+        sv->arena->release(F.x64, F.bx64);
+        sv->arena->release(F.xt, F.bxt);
+        sv->arena->release(F.r32, F.br32);
+        F = SlotMem();
+        return false;
+    }
+    sv->used += need;
+    sv->problem_refs[p] += 1;
+    const ClusterShape &sh = r->ocshape;
+    ClusterJob &J = sv->oc_hj[k];
+    memset(&J, 0, sizeof J);
+    J.rec = p->rec;
+    J.col = p->col;
+    J.val = p->val;
+    J.x64 = M.x64;
+    J.x32 = M.x;
+    J.xt = M.xt;
+    J.b64 = p->b64;
+    J.r32 = M.r32;
+    J.key = make_uint2((unsigned)p->seed, (unsigned)(p->seed >> 32));
+    J.m = (unsigned)p->m;
+    J.n = (unsigned)p->n;
+    J.stream_id = (unsigned)r->ticket;  // each request draws its own row sequence
+    J.uniform = p->uniform;
+    J.sampling = ASYRK_SAMPLE_WEIGHTED;
+    J.shuf_h = shuffle_half_bits(p->m);
+    J.excl = sv->excl ? 1 : 0;
+    J.workers = sh.workers;
+    J.lc = sh.lc;
+    J.nper = sh.nper;
+    J.nper_pad = sh.nper_pad;
+    J.bper = sh.bper;
+    J.gamma = (float)r->gamma;
+    J.refine = refine ? 1 : 0;
+    J.max_inner = sv->max_inner;
+    J.inner_tol = sv->inner_tol;
+    J.j0 = 0;
+    J.max_sweeps = r->max_sweeps;
+    J.tol = r->tol;
+    J.bnorm = p->bnorm;
+    J.meas = J.meas0 = -1.0;
+    J.status = ASYRK_NOT_CONVERGED;
+    // the slot's stream is idle (its previous request was harvested), so these
+    // copies from pageable memory do not wait on other work
+    cudaStream_t st = sv->oc_stream[k];
+    cudaMemcpyAsync(M.x64, r->x0.data(), M.bx64, cudaMemcpyHostToDevice, st);
+    if (has_xt) cudaMemcpyAsync(M.xt, r->xt.data(), M.bxt, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(sv->oc_jobs + k, &J, sizeof J, cudaMemcpyHostToDevice, st);
+    int rc = cluster_launch(p->dtype, sh, sv->oc_jobs, k, st);
+    if (rc == ASYRK_OK && cudaEventRecord(sv->oc_ev[k], st) != cudaSuccess) rc = ASYRK_ECUDA;
+    sv->launches += 1;
+    sv->oc_req[k] = r;
+    r->slot = k;
+    r->t_admit = now_s();
+    if (rc != ASYRK_OK) sv->fatal = rc;  // the engine loop stops the server
+    return true;
+}
+
+static void release_onchip_locked(asyrk_server *sv, int k)
+{
+    Request *r = sv->oc_req[k];
+    asyrk_problem *p = r->p;
+    SlotMem &M = sv->oc_mem[k];
+    sv->arena->release(M.x, M.bx);
+    sv->arena->release(M.x64, M.bx64);
+    sv->arena->release(M.xt, M.bxt);
+    sv->arena->release(M.r32, M.br32);
+    M = SlotMem();
+    size_t give = r->slot_bytes;
+    if (--sv->problem_refs[p] == 0) {
+        sv->problem_refs.erase(p);
+        give += (size_t)p->dev_bytes;
+    }
+    sv->used -= give;
+    sv->oc_req[k] = nullptr;
+    r->slot = -1;
+}
+
+// complete the on-chip requests whose launch has finished; *any: one did
+static int harvest_onchip(asyrk_server *sv, std::unique_lock<std::mutex> &lk, bool *any)
+{
+    *any = false;
+    for (int k = 0; k < sv->oc_slots; ++k) {
+        Request *r = sv->oc_req[k];
+        if (!r) continue;
+        const cudaError_t q = cudaEventQuery(sv->oc_ev[k]);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return cuda_fail(q, "on-chip request", __FILE__, __LINE__);
+        const SlotMem M = sv->oc_mem[k];
+        const unsigned n = (unsigned)r->p->n;
+        const bool refine = r->mode == ASYRK_MODE_REFINE;
+        lk.unlock();
+        // the launch has finished: these copies on the slot's stream run at once
+        cudaStream_t cs = sv->oc_stream[k];
+        ClusterJob J;
+        r->result.resize(n);
+        cudaError_t e = cudaMemcpyAsync(&J, sv->oc_jobs + k, sizeof J, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess && refine) {
+            e = cudaMemcpyAsync(r->result.data(), M.x64, (size_t)n * 8, cudaMemcpyDeviceToHost, cs);
+        } else if (e == cudaSuccess) {
+            sv->oc_x32.resize(n);
+            e = cudaMemcpyAsync(sv->oc_x32.data(), M.x, (size_t)n * 4, cudaMemcpyDeviceToHost, cs);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e == cudaSuccess && !refine)
+            for (unsigned t = 0; t < n; ++t) r->result[t] = (double)sv->oc_x32[t];
+        lk.lock();
+        if (e != cudaSuccess) return cuda_fail(e, "on-chip harvest", __FILE__, __LINE__);
+        asyrk_solve_info &I = r->info;
+        memset(&I, 0, sizeof I);
+        I.workers = r->ocshape.workers;
+        I.subwarp = r->ocshape.G;
+        I.refine_steps = J.outer_steps;
+        I.sweeps = J.sweeps;
+        I.projections = J.sweeps * (int64_t)J.m;
+        I.skipped = (int64_t)J.skipped;
+        I.rel_err = r->xt.empty() ? -1.0 : J.meas;
+        I.rel_res = refine && r->p->bnorm > 0.0 ? sqrt(J.res2) / r->p->bnorm : -1.0;
+        I.j_end = (uint64_t)J.sweeps * J.m;
+        const int status = r->cancelled ? ASYRK_ECANCELED : J.status;
+        release_onchip_locked(sv, k);
+        finish_locked(sv, r, status);
+        sv->oc_completed += 1;
+        *any = true;
+    }
+    return ASYRK_OK;
+}
+
+// complete every shared-step request (in a slot or queued) with `status`
+static void fail_shared_locked(asyrk_server *sv, int status)
 {
     for (int k = 0; k < sv->max_slots; ++k) {
         if (!sv->slot_req[k]) continue;
@@ -326,6 +502,24 @@ static void fail_all_locked(asyrk_server *sv, int status)
     while (!sv->queue.empty()) {
         Request *r = sv->queue.front();
         sv->queue.pop_front();
+        finish_locked(sv, r, status);
+    }
+}
+
+// complete every on-chip request with `status`; launches in flight run to
+// their end first (their memory is released after them)
+static void fail_onchip_locked(asyrk_server *sv, int status)
+{
+    for (int k = 0; k < sv->oc_slots; ++k) {
+        if (!sv->oc_req[k]) continue;
+        cudaStreamSynchronize(sv->oc_stream[k]);
+        Request *r = sv->oc_req[k];
+        release_onchip_locked(sv, k);
+        finish_locked(sv, r, status);
+    }
+    while (!sv->oc_queue.empty()) {
+        Request *r = sv->oc_queue.front();
+        sv->oc_queue.pop_front();
         finish_locked(sv, r, status);
     }
 }
@@ -354,13 +548,19 @@ static int engine_step(asyrk_server *sv, std::unique_lock<std::mutex> &lk, std::
         ASYRK_CK(cudaMalloc((void **)&sv->part, 2 * (size_t)chunks * sizeof(double)));
         sv->part_cap = chunks;
     }
+    // while on-chip launches are in flight the step takes three quarters of the
+    // resident warps, so that none of its blocks waits for an SM that an
+    // on-chip CTA occupies (a step lasts as long as its last block)
+    int oc = 0;
+    for (int k = 0; k < sv->oc_slots; ++k) oc += sv->oc_req[k] ? 1 : 0;
+    const int warps = oc > 0 ? sv->resident_warps / 4 * 3 : sv->resident_warps;
     lk.unlock();
     int st = ASYRK_OK;
     cudaError_t e = cudaMemcpyAsync(sv->d, sv->h.data(), sv->max_slots * sizeof(SysDesc),
                                     cudaMemcpyHostToDevice, sv->s);
     if (e == cudaSuccess)
-        st = launch_engine_step(sv->d, sv->max_slots, chunks, sv->part, sv->resident_warps,
-                                sv->excl, true, sv->s);
+        st = launch_engine_step(sv->d, sv->max_slots, chunks, sv->part, warps, sv->excl, true,
+                                sv->s);
     if (e == cudaSuccess && st == ASYRK_OK)
         e = cudaMemcpyAsync(sv->h.data(), sv->d, sv->max_slots * sizeof(SysDesc),
                             cudaMemcpyDeviceToHost, sv->s);
@@ -437,26 +637,81 @@ static void engine_loop(asyrk_server *sv)
             if (!admit_locked(sv, r, k)) break;
             sv->queue.pop_front();
         }
-        int occupied = 0;
+        int occupied = 0, oc = 0;
         for (int k = 0; k < sv->max_slots; ++k) occupied += sv->slot_req[k] ? 1 : 0;
-        if (occupied > sv->max_active) sv->max_active = occupied;
+        for (int k = 0; k < sv->oc_slots; ++k) oc += sv->oc_req[k] ? 1 : 0;
+        if (occupied + oc > sv->max_active) sv->max_active = occupied + oc;
         if (sv->stop) {
-            fail_all_locked(sv, ASYRK_ECANCELED);
+            fail_shared_locked(sv, sv->fatal != ASYRK_OK ? sv->fatal : ASYRK_ECANCELED);
             break;
         }
         if (occupied == 0) {
-            sv->cv_work.wait_for(lk, std::chrono::milliseconds(50),
-                                 [&] { return sv->stop || !sv->queue.empty(); });
+            if (!sv->queue.empty())  // waits for memory the on-chip requests hold
+                sv->cv_work.wait_for(lk, std::chrono::milliseconds(1), [&] { return sv->stop; });
+            else
+                sv->cv_work.wait_for(lk, std::chrono::milliseconds(50),
+                                     [&] { return sv->stop || !sv->queue.empty(); });
             continue;
         }
         int st = engine_step(sv, lk, done);
         if (st == ASYRK_OK) st = harvest(sv, lk, done);
         if (st != ASYRK_OK) {
             sv->fatal = st;
-            fail_all_locked(sv, st);
             sv->stop = true;
+            sv->cv_oc.notify_all();
+            fail_shared_locked(sv, st);
             break;
         }
+    }
+}
+
+// The on-chip requests' thread: FIFO admission into free on-chip slots while
+// memory allows (each admission launches the request's solve on the slot's
+// stream), and completion of the launches that have finished.
+static void onchip_loop(asyrk_server *sv)
+{
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        int next = 0;
+        while (!sv->oc_queue.empty()) {
+            Request *r = sv->oc_queue.front();
+            if (r->cancelled) {
+                sv->oc_queue.pop_front();
+                finish_locked(sv, r, ASYRK_ECANCELED);
+                continue;
+            }
+            while (next < sv->oc_slots && sv->oc_req[next]) ++next;
+            if (next == sv->oc_slots || !admit_onchip_locked(sv, r, next)) break;
+            sv->oc_queue.pop_front();
+        }
+        int in_flight = 0, shared = 0;
+        for (int k = 0; k < sv->oc_slots; ++k) in_flight += sv->oc_req[k] ? 1 : 0;
+        for (int k = 0; k < sv->max_slots; ++k) shared += sv->slot_req[k] ? 1 : 0;
+        if (in_flight + shared > sv->max_active) sv->max_active = in_flight + shared;
+        if (sv->stop || sv->fatal != ASYRK_OK) {
+            const int why = sv->fatal != ASYRK_OK ? sv->fatal : ASYRK_ECANCELED;
+            sv->stop = true;
+            sv->cv_work.notify_all();
+            fail_onchip_locked(sv, why);
+            break;
+        }
+        if (in_flight == 0) {
+            if (!sv->oc_queue.empty())  // waits for memory the shared step holds
+                sv->cv_oc.wait_for(lk, std::chrono::milliseconds(1), [&] { return sv->stop; });
+            else
+                sv->cv_oc.wait_for(lk, std::chrono::milliseconds(50),
+                                   [&] { return sv->stop || !sv->oc_queue.empty(); });
+            continue;
+        }
+        bool any = false;
+        const int st = harvest_onchip(sv, lk, &any);
+        if (st != ASYRK_OK) {
+            sv->fatal = st;
+            continue;  // stops at the top of the loop
+        }
+        if (!any)  // launches in flight, none finished: look again shortly
+            sv->cv_oc.wait_for(lk, std::chrono::microseconds(20), [&] { return sv->stop; });
     }
 }
 
@@ -476,6 +731,9 @@ extern "C" int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *
     if (!sv) return set_error(ASYRK_ENOMEM, "host allocation failed");
     auto fail = [&](int st) {
         if (sv->s) cudaStreamDestroy(sv->s);
+        for (cudaStream_t x : sv->oc_stream) cudaStreamDestroy(x);
+        for (cudaEvent_t x : sv->oc_ev) cudaEventDestroy(x);
+        cudaFree(sv->oc_jobs);
         cudaFree(sv->d);
         delete sv->arena;
         delete sv;
@@ -494,6 +752,11 @@ extern "C" int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *
     sv->max_slots = o.max_slots > 0 ? o.max_slots : 256;
     if (sv->max_slots > sv->resident_warps) sv->max_slots = sv->resident_warps;
     if (sv->max_slots > BATCH_MAX_SLOTS) sv->max_slots = BATCH_MAX_SLOTS;
+    sv->onchip = o.onchip >= 0;
+    sv->oc_slots = sv->onchip ? SERVER_ONCHIP_SLOTS : 0;
+    sv->oc_req.assign(sv->oc_slots, nullptr);
+    sv->oc_mem.assign(sv->oc_slots, SlotMem());
+    sv->oc_hj.assign(sv->oc_slots, ClusterJob());
     sv->h.assign(sv->max_slots, SysDesc());
     memset(sv->h.data(), 0, sv->max_slots * sizeof(SysDesc));
     sv->slot_req.assign(sv->max_slots, nullptr);
@@ -502,11 +765,30 @@ extern "C" int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *
     if (!sv->arena) return fail(set_error(ASYRK_ENOMEM, "host allocation failed"));
     e = cudaMalloc((void **)&sv->d, sv->max_slots * sizeof(SysDesc));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->s, cudaStreamNonBlocking);
+    if (e == cudaSuccess && sv->oc_slots > 0)
+        e = cudaMalloc((void **)&sv->oc_jobs, sv->oc_slots * sizeof(ClusterJob));
+    for (int k = 0; k < sv->oc_slots && e == cudaSuccess; ++k) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) sv->oc_stream.push_back(st);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) sv->oc_ev.push_back(ev);
+    }
     if (e != cudaSuccess) return fail(cuda_fail(e, "server allocation", __FILE__, __LINE__));
     try {
         sv->th = std::thread(engine_loop, sv);
+        if (sv->oc_slots > 0) sv->oc_th = std::thread(onchip_loop, sv);
     } catch (...) {
-        return fail(set_error(ASYRK_ENOMEM, "could not start the engine thread"));
+        if (sv->th.joinable()) {
+            {
+                std::lock_guard<std::mutex> lock(sv->mu);
+                sv->stop = true;
+                sv->cv_work.notify_all();
+            }
+            sv->th.join();
+        }
+        return fail(set_error(ASYRK_ENOMEM, "could not start the engine threads"));
     }
     *out = sv;
     return ASYRK_OK;
@@ -545,13 +827,35 @@ extern "C" int asyrk_server_submit(asyrk_server *sv, asyrk_problem *p, const dou
         delete r;
         return sv->fatal != ASYRK_OK ? sv->fatal : set_error(ASYRK_EINVAL, "server is stopping");
     }
+    // A problem that fits one CTA's shared memory, and whose Cor. 2 worker cap
+    // a CTA's threads cover to within a factor 2 (one CTA would otherwise run
+    // it slower than the shared step, whose projections take about twice as
+    // long), is solved on-chip.
+    if (sv->onchip) {
+        ClusterShape sh;
+        const int G = engine_subwarp(p, true);
+        if (cluster_shape(p, G, 1, 0, &sh) == ASYRK_OK && sh.fits && sh.C == 1 &&
+            tau_cap_estimate(p->m, p->n) <= 2LL * (CLUSTER_MAX_THREADS / G)) {
+            const long long key = (long long)p->dtype * 64 + G;
+            bool ok = true;
+            if (std::find(sv->oc_prepared.begin(), sv->oc_prepared.end(), key) ==
+                sv->oc_prepared.end()) {
+                ok = cluster_prepare(p->dtype, G, 1) == ASYRK_OK;
+                if (ok) sv->oc_prepared.push_back(key);
+            }
+            if (ok && cluster_check_schedulable(p->dtype, sh) == ASYRK_OK) {
+                r->onchip = true;
+                r->ocshape = sh;
+            }
+        }
+    }
     r->ticket = sv->next_ticket++;
     r->t_submit = now_s();
-    sv->queue.push_back(r);
+    (r->onchip ? sv->oc_queue : sv->queue).push_back(r);
     sv->reqs[r->ticket] = r;
     sv->submitted += 1;
     *ticket = r->ticket;
-    sv->cv_work.notify_one();
+    (r->onchip ? sv->cv_oc : sv->cv_work).notify_one();
     return ASYRK_OK;
 }
 
@@ -585,14 +889,15 @@ extern "C" int asyrk_server_cancel(asyrk_server *sv, uint64_t ticket)
     Request *r = it->second;
     if (r->done) return ASYRK_OK;
     r->cancelled = true;
-    for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q) {
-        if (*q == r) {
-            sv->queue.erase(q);
+    std::deque<Request *> &q = r->onchip ? sv->oc_queue : sv->queue;
+    for (auto it = q.begin(); it != q.end(); ++it) {
+        if (*it == r) {
+            q.erase(it);
             finish_locked(sv, r, ASYRK_ECANCELED);
             break;
         }
     }
-    sv->cv_work.notify_one();
+    (r->onchip ? sv->cv_oc : sv->cv_work).notify_one();
     return ASYRK_OK;
 }
 
@@ -603,10 +908,12 @@ extern "C" int asyrk_server_get_stats(asyrk_server *sv, asyrk_server_stats *st)
     memset(st, 0, sizeof *st);
     st->submitted = sv->submitted;
     st->completed = sv->completed;
-    st->queued = (int64_t)sv->queue.size();
+    st->queued = (int64_t)(sv->queue.size() + sv->oc_queue.size());
     int64_t act = 0;
     for (auto *r : sv->slot_req) act += r ? 1 : 0;
+    for (auto *r : sv->oc_req) act += r ? 1 : 0;
     st->active = act;
+    st->onchip_completed = sv->oc_completed;
     st->iterations = sv->iterations;
     st->kernel_launches = sv->launches;
     st->mem_used = (int64_t)sv->used;
@@ -625,16 +932,22 @@ extern "C" void asyrk_server_destroy(asyrk_server *sv)
         std::lock_guard<std::mutex> lock(sv->mu);
         sv->stop = true;
         sv->cv_work.notify_all();
+        sv->cv_oc.notify_all();
     }
     if (sv->th.joinable()) sv->th.join();
+    if (sv->oc_th.joinable()) sv->oc_th.join();
     {
         std::lock_guard<std::mutex> lock(sv->mu);
-        fail_all_locked(sv, ASYRK_ECANCELED);
+        fail_shared_locked(sv, ASYRK_ECANCELED);
+        fail_onchip_locked(sv, ASYRK_ECANCELED);
         for (auto &kv : sv->reqs) delete kv.second;
         sv->reqs.clear();
     }
     cudaStreamSynchronize(sv->s);
     cudaStreamDestroy(sv->s);
+    for (cudaStream_t x : sv->oc_stream) cudaStreamDestroy(x);
+    for (cudaEvent_t x : sv->oc_ev) cudaEventDestroy(x);
+    cudaFree(sv->oc_jobs);
     cudaFree(sv->d);
     cudaFree(sv->part);
     delete sv->arena;

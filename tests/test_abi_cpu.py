@@ -53,8 +53,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(asyrk.LsqOpts) == 40
     assert ctypes.sizeof(asyrk.BatchInfo) == 64
     assert ctypes.sizeof(asyrk.TuneResult) == 24
-    assert ctypes.sizeof(asyrk.ServerOpts) == 32
-    assert ctypes.sizeof(asyrk.ServerStats) == 88
+    assert ctypes.sizeof(asyrk.ServerOpts) == 40
+    assert ctypes.sizeof(asyrk.ServerStats) == 96
 
 
 def test_abi_version_and_status_strings(lib):

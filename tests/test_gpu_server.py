@@ -7,7 +7,10 @@
     tolerance (both within tol of x*);
   * requests that arrive while others run are admitted as slots free up;
   * the memory budget limits how many run at once, a request bigger than the
-    budget is refused, cancelling and timeouts behave as documented.
+    budget is refused, cancelling and timeouts behave as documented;
+  * requests for problems that fit a CTA's shared memory run on-chip (one CTA
+    launch each, plain or refined) and give the results the shared engine step
+    gives; a running on-chip request that is cancelled ends as cancelled.
 """
 import time
 
@@ -138,7 +141,7 @@ def test_budget_limits_concurrency_and_oversized_requests_are_refused(pool):
 
 def test_cancel_and_timeout(pool):
     systems, probs = pool
-    with asyrk.Server(8 << 30, max_slots=1) as sv:
+    with asyrk.Server(8 << 30, max_slots=1, onchip=False) as sv:  # the queued one stays queued
         running = sv.submit(probs[4], x_true=systems[4].x_true, tol=1e-14, max_sweeps=10**6)
         queued = sv.submit(probs[2], x_true=systems[2].x_true, tol=1e-6)
         st, x, _ = sv.wait(running, systems[4].n, timeout_us=1000)
@@ -161,3 +164,41 @@ def test_destroy_with_pending_work_returns(pool):
     t0 = time.time()
     sv.close()
     assert time.time() - t0 < 30.0
+
+
+def test_onchip_requests_match_the_shared_step(pool):
+    systems, probs = pool
+    jobs = [(0, asyrk.MODE_REFINE, 1e-10), (1, asyrk.MODE_ASYNC, 1e-6), (2, asyrk.MODE_REFINE, 1e-10),
+            (3, asyrk.MODE_ASYNC, 1e-6)]
+    results = {}
+    for onchip in (True, False):
+        with asyrk.Server(8 << 30, onchip=onchip) as sv:
+            ts = [sv.submit(probs[idx], x_true=systems[idx].x_true, tol=tol, mode=mode)
+                  for idx, mode, tol in jobs]
+            out = []
+            for (idx, mode, tol), t in zip(jobs, ts):
+                st, x, info = sv.wait(t, systems[idx].n, timeout_us=60_000_000)
+                assert st == asyrk.OK, (onchip, idx, info.as_dict())
+                assert _err(x, systems[idx]) <= tol * 1.0001
+                assert abs(info.rel_err - _err(x, systems[idx])) <= 1e-3 * _err(x, systems[idx]) + 1e-15
+                if mode == asyrk.MODE_REFINE:
+                    assert info.refine_steps >= 2 and info.rel_res < 1e-8
+                assert info.j_end == info.sweeps * systems[idx].m
+                out.append(x)
+            stt = sv.stats()
+            assert stt["onchip_completed"] == (len(jobs) if onchip else 0)
+            assert stt["mem_used"] == 0 and stt["fatal"] == 0
+            results[onchip] = out
+    for (idx, _, tol), xa, xb in zip(jobs, results[True], results[False]):
+        assert np.linalg.norm(xa - xb) / np.linalg.norm(systems[idx].x_true) <= 2 * tol * 1.0001
+
+
+def test_cancel_a_running_onchip_request(pool):
+    systems, probs = pool
+    with asyrk.Server(8 << 30) as sv:
+        t = sv.submit(probs[2], x_true=systems[2].x_true, tol=1e-14, max_sweeps=20000)
+        time.sleep(0.05)
+        assert sv.cancel(t) == asyrk.OK
+        st, _, info = sv.wait(t, systems[2].n, timeout_us=60_000_000)
+        assert st == asyrk.ECANCELED and info.sweeps >= 1
+        assert sv.stats()["onchip_completed"] == 1
