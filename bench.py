@@ -940,6 +940,22 @@ def run_asyrk(args, dist):
     h_rp, h_col, h_val, h_b, h_xt = (pin(s.row_ptr), pin(s.col), pin(s.val_store), pin(s.b),
                                      pin(s.x_true))
     h_x = torch.zeros(s.n, dtype=torch.float64).pin_memory()
+    # the host link as this machine gives it: the column array from its page-locked
+    # buffer to the device, event-timed (best of 3), before the end-to-end steps
+    h2d_gbs = None
+    if args.e2e_steps > 0:
+        d_col = torch.empty(h_col.numel(), dtype=h_col.dtype, device="cuda")
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            d_col.copy_(h_col, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_c = e0.elapsed_time(e1)
+            best = ms_c if best is None else min(best, ms_c)
+        h2d_gbs = h_col.numel() * h_col.element_size() / (best / 1e3) / 1e9
+        del d_col
     e2e_t, e2e_proj = 0.0, 0
     split = {"create_s": 0.0, "solve_s": 0.0, "destroy_s": 0.0}
     for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):  # first round warms up
@@ -970,7 +986,7 @@ def run_asyrk(args, dist):
            "d2h_bytes_per_step": int(d2h),
            "what": "asyrk_create from pinned host CSR + asyrk_solve (host x0 -> host x) + destroy",
            "ms_per_step_split": {k: 1e3 * v / max(1, args.e2e_steps) for k, v in split.items()},
-           "host_affinity": affinity}
+           "host_affinity": affinity, "h2d_probe_gbs": h2d_gbs}
 
     cpu = None
     cpu_mt = None
