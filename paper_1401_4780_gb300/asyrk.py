@@ -584,7 +584,13 @@ class Problem:
 
 
 class Batch:
-    """Owns one asyrk_batch handle over a list of Problem objects."""
+    """Owns one asyrk_batch handle over a list of Problem objects.
+
+    engine: ENGINE_AUTO (members that fit a CTA's shared memory on-chip, the rest in
+    the global-iterate engine, both at once), ENGINE_GLOBAL or ENGINE_ONCHIP (every
+    member on-chip, else EINVAL); cluster_max: CTAs per on-chip cluster at most
+    (0: one); workers: on-chip workers per member at most (0: the Cor. 2 estimate).
+    """
 
     def __init__(self, problems, stream=None, graph=True, row_exclusion=0,
                  sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW, engine=0, cluster_max=0,
@@ -624,7 +630,11 @@ class Batch:
 
 
 class Server:
-    """Owns one asyrk_server (continuous batching of solve requests)."""
+    """Owns one asyrk_server (continuous batching of solve requests).
+
+    onchip: requests whose problem fits a CTA's shared memory are solved on-chip,
+    one CTA launch each, beside the shared engine step (False: all in the step).
+    """
 
     def __init__(self, mem_budget_bytes, max_slots=0, row_exclusion=0, inner_tol=0.0,
                  max_inner_sweeps=0, onchip=True):
