@@ -74,6 +74,8 @@ def _bind(path):
     lib.oracle_validate.restype = ctypes.c_int
     lib.oracle_row_weights.argtypes = [i64, P, P, P]
     lib.oracle_row_weights.restype = f64
+    lib.oracle_exact_sum.argtypes = [i64, P]
+    lib.oracle_exact_sum.restype = f64
     lib.oracle_alias_build.argtypes = [i64, P, f64, P, P]
     lib.oracle_alias_build.restype = ctypes.c_int
     lib.oracle_draw_rows.argtypes = [u64, u32, u64, i64, i64, P, P, ctypes.c_int, P]
@@ -151,8 +153,16 @@ def philox4x32_10(ctr, key):
     return out
 
 
+def exact_sum(v):
+    """The sum of finite values v_i >= 0, exact until one final rounding to the
+    nearest double (ties to even)."""
+    a = np.ascontiguousarray(v, dtype=np.float64)
+    return float(_load().oracle_exact_sum(a.shape[0], _p(a)))
+
+
 def row_weights(m, row_ptr, val):
-    """w_i = ||a_i||^2 (CSR order) and F = ||A||_F^2 (index order), FP64."""
+    """w_i = ||a_i||^2 (FP64, CSR order) and F = ||A||_F^2, the w_i's exact sum
+    rounded once."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     v = np.ascontiguousarray(val, dtype=np.float64)
     w = np.zeros(m, dtype=np.float64)

@@ -28,8 +28,9 @@
  * with Philox4x32-10 written from Salmon, Moraes, Dror and Shaw, "Parallel
  * random numbers: as easy as 1, 2, 3" (SC'11), and an alias table (Walker's
  * method) built as follows:
- *   - F = ||A||_F^2 is summed in blocks of 2048 consecutive rows (each block in
- *     index order, then the block sums in order);
+ *   - F = ||A||_F^2 is the exact sum of the w_i rounded once to the nearest
+ *     double (ties to even): the w_i are added in index order into a wide
+ *     fixed-point integer that loses nothing, and only the total is rounded;
  *   - integer masses M_i = floor(((w_i m) / F) 2^32) (FP64, in that order);
  *     one bucket holds U = 2^32; the D = m U - sum M_i units the floors lose
  *     go one per row from row 0 on (D/m to every row first when D >= m), and
@@ -71,14 +72,12 @@
  *
  * Arithmetic is round-to-nearest FP64 in the order written, with no FMA
  * contraction (the build passes -ffp-contract=off): w_i sums val^2 in CSR
- * order, F sums w_i in index order, a_i^T x sums in CSR order.
+ * order, a_i^T x sums in CSR order; F alone is exact before its one rounding.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
-
-#define ORACLE_F_BLOCK 2048
 
 #define OR_OK 0
 #define OR_EINVAL (-1)
@@ -147,7 +146,79 @@ int oracle_validate(int64_t m, int64_t n, const int64_t *row_ptr,
     return OR_OK;
 }
 
-/* w_i = ||a_i||^2 in CSR order; returns F = ||A||_F^2 summed in index order. */
+/* ------------------------------------------------------------------ */
+/* Exact sum of non-negative doubles.  Every finite double is an        */
+/* integer multiple of 2^-1074 below 2^1024, so the sum of fewer than   */
+/* 2^31 of them is an integer (in units of 2^-1074) of at most 2129     */
+/* bits: EXACT_DIGITS base-2^32 digits, least significant first, hold   */
+/* it with room to spare.  Nothing is rounded until exact_round.        */
+/* ------------------------------------------------------------------ */
+#define EXACT_DIGITS 68
+
+/* digits += v, for a finite v >= 0 */
+static void exact_add(uint32_t *digits, double v)
+{
+    if (v == 0.0) return;
+    int e;
+    const double f = frexp(v, &e);                  /* v = f 2^e, 1/2 <= f < 1 */
+    uint64_t mant = (uint64_t)ldexp(f, 53);         /* v = mant 2^(e - 53), exactly */
+    int pos = e - 53 + 1074;                        /* weight of mant's last bit, from 2^-1074 */
+    while (pos < 0) { mant >>= 1; ++pos; }          /* subnormal v: the bits shifted out are 0 */
+    const int q = pos / 32, r = pos % 32;
+    /* the three base-2^32 digits of mant 2^r, added at digit q with carries */
+    uint32_t part[3];
+    part[0] = (uint32_t)(mant << r);
+    part[1] = (uint32_t)(r == 0 ? mant >> 32 : mant >> (32 - r));
+    part[2] = (uint32_t)(r == 0 ? 0 : mant >> (64 - r));
+    uint64_t carry = 0;
+    for (int k = q; k < EXACT_DIGITS; ++k) {
+        const uint64_t t = (uint64_t)digits[k] + (k - q < 3 ? part[k - q] : 0) + carry;
+        digits[k] = (uint32_t)t;
+        carry = t >> 32;
+        if (k - q >= 2 && carry == 0) break;
+    }
+}
+
+/* bit b of the digit string */
+static int exact_bit(const uint32_t *digits, int b)
+{
+    return (int)((digits[b / 32] >> (b % 32)) & 1u);
+}
+
+/* The digits' value, units of 2^-1074, rounded to the nearest double, ties to
+ * even; +inf when it is 2^1024 or more after rounding. */
+static double exact_round(const uint32_t *digits)
+{
+    int top = -1;                                   /* highest set bit */
+    for (int b = 32 * EXACT_DIGITS - 1; b >= 0; --b)
+        if (exact_bit(digits, b)) { top = b; break; }
+    if (top < 0) return 0.0;
+    if (top < 53) {                                 /* fewer than 54 bits: exact */
+        uint64_t v = 0;
+        for (int b = top; b >= 0; --b) v = 2 * v + (uint64_t)exact_bit(digits, b);
+        return ldexp((double)v, -1074);
+    }
+    const int s = top - 52;                         /* the 53 kept bits are top..s */
+    uint64_t mant = 0;
+    for (int b = top; b >= s; --b) mant = 2 * mant + (uint64_t)exact_bit(digits, b);
+    const int guard = exact_bit(digits, s - 1);
+    int sticky = 0;
+    for (int b = s - 2; b >= 0 && !sticky; --b) sticky = exact_bit(digits, b);
+    if (guard && (sticky || (mant & 1u))) ++mant;   /* round half to even */
+    return ldexp((double)mant, s - 1074);           /* mant <= 2^53: exact, or +inf */
+}
+
+/* The correctly rounded sum of n finite values v_i >= 0 (n < 2^31). */
+double oracle_exact_sum(int64_t n, const double *v)
+{
+    uint32_t digits[EXACT_DIGITS];
+    memset(digits, 0, sizeof digits);
+    for (int64_t i = 0; i < n; ++i) exact_add(digits, v[i]);
+    return exact_round(digits);
+}
+
+/* w_i = ||a_i||^2 in CSR order; returns F = ||A||_F^2, the exact sum of the
+ * w_i rounded once. */
 double oracle_row_weights(int64_t m, const int64_t *row_ptr, const double *val,
                           double *w)
 {
@@ -156,16 +227,7 @@ double oracle_row_weights(int64_t m, const int64_t *row_ptr, const double *val,
         for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += val[k] * val[k];
         w[i] = s;
     }
-    /* F: the sum of each block of ORACLE_F_BLOCK consecutive w_i in index
-     * order, then the block sums in block order */
-    double F = 0.0;
-    for (int64_t b0 = 0; b0 < m; b0 += ORACLE_F_BLOCK) {
-        const int64_t b1 = b0 + ORACLE_F_BLOCK < m ? b0 + ORACLE_F_BLOCK : m;
-        double part = 0.0;
-        for (int64_t i = b0; i < b1; ++i) part += w[i];
-        F += part;
-    }
-    return F;
+    return oracle_exact_sum(m, w);
 }
 
 /* The alias table (see the header): integer masses M_i = floor(q_i 2^32) with

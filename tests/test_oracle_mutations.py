@@ -4,6 +4,7 @@ Each case rewrites one expression of ``oracle/asyrk_oracle.c`` in a temporary
 copy, builds it, runs the oracle's Python API on that build and asserts that the
 pin named beside the mistake fails.  The real oracle is never modified.
 """
+import math
 import os
 import subprocess
 
@@ -147,6 +148,23 @@ def pin_lsq_spectrum():
     return got.shape == want.shape and np.allclose(got, want, rtol=1e-12, atol=1e-12 * want.max())
 
 
+def pin_frobenius_exact():
+    # F = ||A||_F^2 (Section 1's row probabilities divide by it) is the exact
+    # sum of the w_i, rounded once: checked against Python's correctly rounded
+    # math.fsum on weights whose plain or blocked running sums round away
+    # thousands of small terms
+    m = 6000
+    val = np.full(m, 2.0**-27)          # w_i = 2^-54: below half an ulp of 1
+    val[0] = 1.0
+    val[2500] = 3.0
+    row_ptr = np.arange(m + 1, dtype=np.int64)
+    w, F = oracle.row_weights(m, row_ptr, val)
+    # a tie broken by one bit far below it: 1 + 2^-53 + 2^-1074 rounds up
+    tie = np.array([1.0, 2.0**-53, 2.0**-1074])
+    return (F == math.fsum(w) and oracle.exact_sum(w[::-1]) == F
+            and oracle.exact_sum(tie) == math.fsum(tie) == 1.0 + 2.0**-52)
+
+
 MUTATIONS = [
     ("dropped gamma", "double s = gamma * r / w[i];", "double s = r / w[i];", pin_step_identity),
     ("sign of b", "double r = dot - b[i];", "double r = dot + b[i];", pin_step_identity),
@@ -190,6 +208,17 @@ MUTATIONS = [
      pin_lsq_spectrum),
     ("least squares: right side over the wrong b",
      "s += tval[p] * b[trow[p]];", "s += tval[p] * b[p - cstart[j]];", pin_lsq_solution),
+    ("F summed by a plain running sum", "return oracle_exact_sum(m, w);",
+     "double F = 0.0;\n    for (int64_t i = 0; i < m; ++i) F += w[i];\n    return F;",
+     pin_frobenius_exact),
+    ("F summed in blocks of 2048 rows", "return oracle_exact_sum(m, w);",
+     "double F = 0.0;\n    for (int64_t b0 = 0; b0 < m; b0 += 2048) {\n"
+     "        double part = 0.0;\n"
+     "        for (int64_t i = b0; i < m && i < b0 + 2048; ++i) part += w[i];\n"
+     "        F += part;\n    }\n    return F;",
+     pin_frobenius_exact),
+    ("exact sum drops the sticky bit", "sticky = exact_bit(digits, b);", "sticky = 0;",
+     pin_frobenius_exact),
     ("stop test on wrong measure", "if (meas <= tol) status = OR_OK;\n    }",
      "if (meas <= 1e3 * tol) status = OR_OK;\n    }", pin_solver_reaches_tolerance),
 ]
