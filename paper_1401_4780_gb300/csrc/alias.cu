@@ -4,8 +4,14 @@
 // Section 1) through Walker's alias table.  The table is defined by one
 // sequential sweep (the header of asyrk.h states it); this file evaluates the
 // same table in parallel:
-//   * F sums blocks of 2048 consecutive w_i in index order, then the block sums
-//     in order (the same order as the definition, so the same FP64 value);
+//   * F is the exact sum of the w_i rounded once to the nearest double (ties to
+//     even).  Every finite double is an integer multiple of 2^-1074 below
+//     2^1024, so the sum is an integer of at most 2129 bits in those units: each
+//     thread splits its values into base-2^32 digits and adds them into 64-bit
+//     digit counters (registers, then shared memory, then one global
+//     accumulator per sum) with integer atomics, which are exact in any order;
+//     one thread then propagates the carries and rounds.  ||b||^2 is formed the
+//     same way from the b_i^2;
 //   * integer masses M_i = floor(((w_i m) / F) 2^32), corrected so that they add
 //     up to m U exactly (U = 2^32, one bucket);
 //   * lights (M < U) and heavies (M >= U) are compacted in index order by one
@@ -24,36 +30,143 @@ namespace asyrk {
 
 namespace {
 
-constexpr int F_BLOCK = 2048;
 constexpr long long UNIT = 1LL << 32;
 
 inline unsigned blocks_for(int64_t count) { return (unsigned)((count + 255) / 256); }
 
-// one CTA per block of F_BLOCK rows: the block's values are staged in shared
-// memory by coalesced loads, then one thread adds them in index order
-__global__ void __launch_bounds__(256) k_block_sums(const double *__restrict__ v, int64_t m,
-                                                    int square, double *__restrict__ part)
+// ---------------------------------------------------------------------------
+// Exact sums of non-negative doubles.  Digit k of an accumulator counts units
+// of 2^(32k - 1074); XDIG digits cover 2^-1074 .. 2^1102, room for the sum of
+// up to 2^31 values below 2^1024.  A digit counter takes at most one 32-bit
+// part per value, so it stays below 2^63 for fewer than 2^31 values.  Word
+// XDIG flags a value that is not finite.
+// ---------------------------------------------------------------------------
+constexpr int XDIG = 68;
+constexpr int XWORDS = XDIG + 1;
+constexpr int XWIN = 6;  // digits a thread keeps in registers
+
+// v = man 2^(pos - 1074) (man < 2^53); returns the digit of man's lowest bit
+// and the three base-2^32 parts of man shifted to it; -1 for inf / NaN
+__device__ __forceinline__ int split_exact(double v, unsigned &d0, unsigned &d1, unsigned &d2)
 {
-    __shared__ double sh[F_BLOCK];
-    const int64_t lo = (int64_t)blockIdx.x * F_BLOCK;
-    const int len = (int)(m - lo < F_BLOCK ? m - lo : F_BLOCK);
-    for (int i = threadIdx.x; i < len; i += 256) {
-        const double x = v[lo + i];
-        sh[i] = square ? __dmul_rn(x, x) : x;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    if (ex == 0x7ff) return -1;
+    unsigned long long man = bits & ((1ULL << 52) - 1);
+    int pos = 0;  // subnormal (or zero): man 2^-1074
+    if (ex != 0) {
+        man |= 1ULL << 52;
+        pos = ex - 1;
     }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    double s = 0.0;
-    for (int i = 0; i < len; ++i) s = __dadd_rn(s, sh[i]);
-    part[blockIdx.x] = s;
+    const int r = pos & 31;
+    d0 = (unsigned)(man << r);
+    d1 = (unsigned)(r ? man >> (32 - r) : man >> 32);
+    d2 = r ? (unsigned)(man >> (64 - r)) : 0u;
+    return pos >> 5;
 }
 
-__global__ void k_seq_sum(const double *__restrict__ part, int64_t nb, double *__restrict__ out)
+// acc[0..XWORDS) += the digits of v[i] (squared when square) for i < n; one
+// CTA's counters are gathered in shared memory before the global atomics.
+__global__ void __launch_bounds__(256) k_exact_accumulate(const double *__restrict__ v, int64_t n,
+                                                          int square,
+                                                          unsigned long long *__restrict__ acc)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int64_t b = 0; b < nb; ++b) s = __dadd_rn(s, part[b]);
-    *out = s;
+    __shared__ unsigned long long sh[XWORDS];
+    for (int k = threadIdx.x; k < XWORDS; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    // a window of XWIN digits in registers, placed at the thread's first value
+    unsigned long long win[XWIN];
+#pragma unroll
+    for (int k = 0; k < XWIN; ++k) win[k] = 0;
+    int base = -1;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double x = v[i];
+        if (square) x = __dmul_rn(x, x);
+        unsigned d0, d1, d2;
+        const int q = split_exact(x, d0, d1, d2);
+        if (q < 0) {
+            bad = true;
+            continue;
+        }
+        if (base < 0) base = min(max(q - 1, 0), XDIG - XWIN);
+        const int o = q - base;
+        if (o >= 0 && o + 2 < XWIN) {
+#pragma unroll
+            for (int k = 0; k < XWIN; ++k)
+                win[k] += k == o ? d0 : k == o + 1 ? d1 : k == o + 2 ? d2 : 0u;
+        } else {
+            atomicAdd(&sh[q], (unsigned long long)d0);
+            atomicAdd(&sh[q + 1], (unsigned long long)d1);
+            atomicAdd(&sh[q + 2], (unsigned long long)d2);
+        }
+    }
+    if (base >= 0) {
+#pragma unroll
+        for (int k = 0; k < XWIN; ++k)
+            if (win[k]) atomicAdd(&sh[base + k], win[k]);
+    }
+    if (bad) atomicOr(&sh[XDIG], 1ULL);
+    __syncthreads();
+    for (int k = threadIdx.x; k < XWORDS; k += blockDim.x)
+        if (sh[k]) atomicAdd(&acc[k], sh[k]);
+}
+
+// out[s] = accumulator s rounded to the nearest double, ties to even (inf
+// from 2^1024 on, NaN when a value was not finite); one thread per sum
+__global__ void k_exact_round(const unsigned long long *__restrict__ acc, int count,
+                              double *__restrict__ out)
+{
+    const int s = threadIdx.x;
+    if (s >= count) return;
+    const unsigned long long *a = acc + (size_t)s * XWORDS;
+    if (a[XDIG]) {
+        out[s] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    unsigned dig[XDIG];
+    unsigned long long carry = 0;
+    for (int k = 0; k < XDIG; ++k) {
+        const unsigned long long t = a[k] + carry;  // a[k] < 2^63, carry < 2^32
+        dig[k] = (unsigned)t;
+        carry = t >> 32;
+    }
+    int top = XDIG - 1;
+    while (top >= 0 && dig[top] == 0) --top;
+    if (top < 0) {
+        out[s] = 0.0;
+        return;
+    }
+    const int nbits = 32 * top + 32 - __clz(dig[top]);  // bit length of the sum
+    if (nbits <= 53) {
+        // below 2^53 units of 2^-1074: the bit pattern of the double is the
+        // integer itself (subnormal below 2^52, exponent field 1 above)
+        const unsigned long long V =
+            (unsigned long long)dig[0] | (top >= 1 ? (unsigned long long)dig[1] << 32 : 0ULL);
+        out[s] = __longlong_as_double((long long)V);
+        return;
+    }
+    const int sh = nbits - 53;  // bits [sh, nbits) are kept
+    // the 53 kept bits, the guard bit below them and whether anything lower is set
+    auto bit = [&](int b) -> unsigned { return (dig[b >> 5] >> (b & 31)) & 1u; };
+    unsigned long long man = 0;
+    for (int b = nbits - 1; b >= sh; --b) man = (man << 1) | bit(b);
+    const unsigned guard = bit(sh - 1);
+    bool sticky = false;
+    for (int k = 0; k < ((sh - 1) >> 5) && !sticky; ++k) sticky = dig[k] != 0;
+    if (!sticky && ((sh - 1) & 31)) sticky = (dig[(sh - 1) >> 5] & ((1u << ((sh - 1) & 31)) - 1u)) != 0;
+    if (guard && (sticky || (man & 1ULL))) ++man;
+    int e = sh + 1;  // biased exponent of man 2^(sh - 1074), man in [2^52, 2^53)
+    if (man >> 53) {
+        man >>= 1;
+        ++e;
+    }
+    if (e >= 0x7ff) {
+        out[s] = __longlong_as_double(0x7ff0000000000000LL);
+        return;
+    }
+    out[s] = __longlong_as_double((long long)(((unsigned long long)e << 52) | (man & ((1ULL << 52) - 1))));
 }
 
 __global__ void k_differs(const double *__restrict__ w, int64_t m, unsigned *__restrict__ flag)
@@ -241,19 +354,22 @@ struct Tmp {
 int row_totals_and_alias(asyrk_problem *p, cudaStream_t s)
 {
     const int64_t m = p->m;
-    const int64_t nb = (m + F_BLOCK - 1) / F_BLOCK;
     Tmp t;
-    double *part, *sums;  // sums: F, ||b||^2
+    double *sums;  // sums: F, ||b||^2
     unsigned *differs;
-    unsigned long long *acc;  // sum of masses, max mass, first row of max mass
+    unsigned long long *acc;    // sum of masses, max mass, first row of max mass
+    unsigned long long *exact;  // the two exact accumulators
     int st;
-    if ((st = t.alloc(&part, (size_t)nb)) || (st = t.alloc(&sums, 2)) ||
-        (st = t.alloc(&differs, 1)) || (st = t.alloc(&acc, 3)))
+    if ((st = t.alloc(&sums, 2)) || (st = t.alloc(&differs, 1)) || (st = t.alloc(&acc, 3)) ||
+        (st = t.alloc(&exact, 2 * XWORDS)))
         return st;
-    k_block_sums<<<(unsigned)nb, 256, 0, s>>>(p->w64, m, 0, part);
-    k_seq_sum<<<1, 32, 0, s>>>(part, nb, sums);
-    k_block_sums<<<(unsigned)nb, 256, 0, s>>>(p->b64, m, 1, part);
-    k_seq_sum<<<1, 32, 0, s>>>(part, nb, sums + 1);
+    // enough CTAs to fill the GPU; each thread sweeps its share in registers
+    const int64_t want = (m + 255) / 256;
+    const unsigned gx = (unsigned)(want < 4LL * p->sm_count ? want : 4LL * p->sm_count);
+    ASYRK_CK(cudaMemsetAsync(exact, 0, 2 * XWORDS * sizeof(unsigned long long), s));
+    k_exact_accumulate<<<gx, 256, 0, s>>>(p->w64, m, 0, exact);
+    k_exact_accumulate<<<gx, 256, 0, s>>>(p->b64, m, 1, exact + XWORDS);
+    k_exact_round<<<1, 32, 0, s>>>(exact, 2, sums);
     ASYRK_CK(cudaMemsetAsync(differs, 0, sizeof(unsigned), s));
     k_differs<<<blocks_for(m), 256, 0, s>>>(p->w64, m, differs);
     ASYRK_CK(cudaGetLastError());

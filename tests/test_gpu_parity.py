@@ -8,6 +8,8 @@
   * residual ||b - A x||/||b|| in FP64 matches the oracle's to 1e-12;
   * resuming from a saved position reproduces the uninterrupted run exactly.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -53,6 +55,7 @@ def test_row_sequence_is_bit_exact(kind):
     samp = oracle.Sampler(s.m, s.row_ptr, s.val64)
     with asyrk.Problem.from_system(s) as p:
         assert p.stats()["uniform"] == samp.uniform
+        assert p.stats()["frob2"] == samp.F == math.fsum(samp.w)
         for j0, count, stream in [(0, 1_000_000, 0), (2**32 - 500, 1000, 0), (12345, 5000, 7)]:
             got = p.draw_rows(j0, count, stream)
             want = oracle.draw_rows(seed, stream, j0, count, samp.thr, samp.alias, samp.uniform)
@@ -186,8 +189,61 @@ def test_alias_table_built_on_the_gpu_matches_the_oracle(kind):
     samp = oracle.Sampler(m, row_ptr, val)
     with asyrk.Problem(m, m, row_ptr, col, val, asyrk.F64, b, seed=77) as p:
         assert p.stats()["uniform"] == samp.uniform
-        assert p.stats()["frob2"] == samp.F  # the same blocked FP64 sum
+        # F is the w_i's exact sum rounded once, on both sides
+        assert p.stats()["frob2"] == samp.F == math.fsum(samp.w)
         for j0, count in [(0, 300_000), (2**33 + 5, 10_000)]:
             np.testing.assert_array_equal(
                 p.draw_rows(j0, count, 3),
                 oracle.draw_rows(77, 3, j0, count, samp.thr, samp.alias, samp.uniform))
+
+
+@pytest.mark.parametrize("kind", ["tiny_rows_beside_unit_rows", "wide_dynamic_range",
+                                  "subnormal_weights"])
+def test_frobenius_norm_is_the_correctly_rounded_sum(kind):
+    # Section 1's probabilities divide by F = ||A||_F^2; both sides take it as
+    # the exact sum of the w_i rounded once, so it matches Python's correctly
+    # rounded math.fsum bit for bit, where any running or blocked FP64 sum
+    # (the GPU's reduction order included) would round away the small rows
+    rng = np.random.default_rng(21)
+    m = 300_000
+    if kind == "tiny_rows_beside_unit_rows":
+        val = np.full(m, 2.0**-27)            # w_i = 2^-54, half an ulp of 1 / 2
+        val[rng.choice(m, 40, replace=False)] = 1.0
+    elif kind == "wide_dynamic_range":
+        val = np.exp(60.0 * rng.standard_normal(m))  # weights from ~1e-200 to ~1e200
+    else:
+        val = np.full(m, 2.0**-530)           # w_i = 2^-1060: subnormal
+        val[::7] = 2.0**-520
+    row_ptr = np.arange(m + 1, dtype=np.int64)
+    col = (np.arange(m) % 1000).astype(np.int32)
+    b = val.copy()
+    samp = oracle.Sampler(m, row_ptr, val)
+    assert samp.F == math.fsum(samp.w)
+    with asyrk.Problem(m, 1000, row_ptr, col, val, asyrk.F64, b, seed=5) as p:
+        assert p.stats()["frob2"] == samp.F
+        assert p.stats()["uniform"] == samp.uniform
+        np.testing.assert_array_equal(
+            p.draw_rows(0, 200_000, 1),
+            oracle.draw_rows(5, 1, 0, 200_000, samp.thr, samp.alias, samp.uniform))
+
+
+@pytest.mark.parametrize("subwarp", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_async_fp32_kernel_with_one_worker_matches_the_oracle(dtype, subwarp):
+    # the kernel the large asynchronous workload runs -- FP32 iterate, FP32 b
+    # and 1/||a_i||^2 from the row record, row exclusion on -- with a single
+    # worker applies the projections in order: after two sweeps its iterate is
+    # the oracle's sequential RK iterate (Eq. (2)) on the same row sequence, to
+    # FP32 accuracy; ragged rows of 1..70 entries exercise the chunk tails and
+    # the rows longer than a worker keeps in registers
+    s = synth.make_system(3000, 800, (1, 70), 515, row_norms="lognormal", value_dtype=dtype)
+    seed = synth.solver_seed(s.seed)
+    with asyrk.Problem.from_system(s) as p:
+        x = np.zeros(s.n)
+        st, info = p.solve(x, tol=0.0, max_sweeps=2, mode=asyrk.MODE_ASYNC, workers=1,
+                           subwarp=subwarp)
+        assert st == asyrk.OK  # tol = 0: the sweep budget ends the solve
+        assert info.workers == 1 and info.subwarp == subwarp and info.skipped == 0
+        assert info.projections == 2 * s.m
+    xo = _oracle_steps(s, seed, 2 * s.m)
+    assert _rel(x, xo) <= 2e-5
