@@ -38,8 +38,9 @@
  *     alias[bucket], where (thr, alias) is the alias table (Walker's method)
  *     of the row weights w_i = ||a_i||^2 (unused when all weights are
  *     bit-identical), built on the GPU and defined by one sweep:
- *     F = ||A||_F^2 sums blocks of 2048 consecutive w_i in index order, then
- *     the block sums in order; integer masses M_i = floor(((w_i m) / F) 2^32)
+ *     F = ||A||_F^2 is the exact sum of the w_i rounded once to the nearest
+ *     double, ties to even (so it does not depend on any order of
+ *     summation); integer masses M_i = floor(((w_i m) / F) 2^32)
  *     (one bucket is U = 2^32 units), the D = m U - sum M_i units lost to the
  *     floors added one per row from row 0 on (D / m to every row first when
  *     D >= m), an overshoot (D < 0) taken off the first row of largest mass;
@@ -187,7 +188,7 @@ typedef struct asyrk_problem_stats {
     int64_t nnz_padded;       /* stored entries after padding rows to 4-aligned starts */
     int64_t max_row_len;      /* mu = max_i ||a_i||_0 (Section 1 notation)           */
     int64_t device_bytes;     /* device memory held by the handle                    */
-    double frob2;             /* ||A||_F^2 in FP64, summed as the alias table states */
+    double frob2;             /* ||A||_F^2: the w_i's exact sum, rounded once        */
     int32_t dtype;            /* asyrk_dtype of the stored values                   */
     int32_t uniform;          /* 1: all row weights bit-identical, no alias table    */
     uint64_t seed;            /* Philox key                                          */
@@ -375,6 +376,14 @@ typedef struct asyrk_server_opts {
     int64_t max_inner_sweeps;  /* REFINE inner sweeps per outer step at most (0: 60) */
     int32_t onchip;            /* >= 0: requests whose problem fits a CTA's shared
                                   memory are solved on-chip (default); -1: never     */
+    int32_t reserved;          /* must be 0                                          */
+    double admit_load;         /* shared-step admission: queued requests are admitted
+                                  in arrival order while the warp demands of the
+                                  requests in the step (each its Cor. 2 worker cap
+                                  in warps, at most the resident warps) add up to at
+                                  most admit_load x the resident warps; one request
+                                  is always admitted.  0: 1.0; < 0: no limit (only
+                                  slots and memory bound admission)                 */
 } asyrk_server_opts;
 
 typedef struct asyrk_server_stats {
@@ -387,7 +396,7 @@ typedef struct asyrk_server_stats {
     int32_t max_slots;
     int32_t max_active;        /* most requests in flight at once so far             */
     int32_t fatal;             /* first hard error of the engine, or OK              */
-    int32_t reserved;
+    int32_t max_active_shared; /* most requests in the shared engine step at once    */
     int64_t onchip_completed;  /* requests solved on-chip so far                     */
 } asyrk_server_stats;
 
