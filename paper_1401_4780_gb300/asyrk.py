@@ -203,7 +203,8 @@ class BatchInfo(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("row_exclusion", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("max_inner_sweeps", ctypes.c_int64), ("onchip", ctypes.c_int32)]
+                ("max_inner_sweeps", ctypes.c_int64), ("onchip", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("admit_load", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -213,7 +214,7 @@ class ServerStats(ctypes.Structure):
                 ("mem_used", ctypes.c_int64), ("mem_budget", ctypes.c_int64),
                 ("arena_reserved", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("max_active", ctypes.c_int32), ("fatal", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("onchip_completed", ctypes.c_int64)]
+                ("max_active_shared", ctypes.c_int32), ("onchip_completed", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -390,11 +391,12 @@ def asyrk_batch_destroy(b):
 
 
 def asyrk_server_create(mem_budget_bytes, max_slots=0, row_exclusion=0, inner_tol=0.0,
-                        max_inner_sweeps=0, onchip=True):
+                        max_inner_sweeps=0, onchip=True, admit_load=0.0):
     h = ctypes.c_void_p()
     o = ServerOpts(mem_budget_bytes=int(mem_budget_bytes), max_slots=max_slots,
                    row_exclusion=row_exclusion, inner_tol=inner_tol,
-                   max_inner_sweeps=max_inner_sweeps, onchip=0 if onchip else -1)
+                   max_inner_sweeps=max_inner_sweeps, onchip=0 if onchip else -1,
+                   admit_load=float(admit_load))
     st = load().asyrk_server_create(ctypes.byref(h), ctypes.byref(o))
     return st, h
 
@@ -634,12 +636,15 @@ class Server:
 
     onchip: requests whose problem fits a CTA's shared memory are solved on-chip,
     one CTA launch each, beside the shared engine step (False: all in the step).
+    admit_load: the shared step admits queued requests in arrival order while the
+    warp demands of those in the step add up to at most admit_load x the resident
+    warps (0: 1.0; < 0: no limit).
     """
 
     def __init__(self, mem_budget_bytes, max_slots=0, row_exclusion=0, inner_tol=0.0,
-                 max_inner_sweeps=0, onchip=True):
+                 max_inner_sweeps=0, onchip=True, admit_load=0.0):
         st, h = asyrk_server_create(mem_budget_bytes, max_slots, row_exclusion, inner_tol,
-                                    max_inner_sweeps, onchip)
+                                    max_inner_sweeps, onchip, admit_load)
         if st != OK:
             raise AsyrkError(st, "asyrk_server_create")
         self.h = h

@@ -136,6 +136,7 @@ struct Request {
     size_t slot_bytes = 0;
     bool onchip = false;   // solved by one CTA (ocshape) instead of the shared engine step
     ClusterShape ocshape;
+    long long demand = 0;  // warps the shared step would give it alone (its Cor. 2 cap)
     asyrk_solve_info info;
 };
 
@@ -165,6 +166,8 @@ struct asyrk_server {
     int resident_warps = 0;
     double inner_tol = 1e-3;
     int64_t max_inner = 60;
+    double admit_load = 1.0;   // <= 0: admission bounded by slots and memory only
+    int max_active_shared = 0;
     cudaStream_t s = nullptr;
     SysDesc *d = nullptr;
     std::vector<SysDesc> h;
@@ -527,8 +530,12 @@ static void fail_onchip_locked(asyrk_server *sv, int status)
 // one engine step over the occupied slots, GPU work done without the lock
 static int engine_step(asyrk_server *sv, std::unique_lock<std::mutex> &lk, std::vector<int> &done)
 {
+    // the descriptors up to the last occupied slot are all the step reads
+    int hi = 0;
+    for (int k = 0; k < sv->max_slots; ++k)
+        if (sv->slot_req[k]) hi = k + 1;
     int chunks = 0;
-    for (int k = 0; k < sv->max_slots; ++k) {
+    for (int k = 0; k < hi; ++k) {
         SysDesc &D = sv->h[k];
         D.chunk0 = chunks;
         if (!sv->slot_req[k]) {
@@ -550,20 +557,20 @@ static int engine_step(asyrk_server *sv, std::unique_lock<std::mutex> &lk, std::
     }
     // while on-chip launches are in flight the step takes three quarters of the
     // resident warps, so that none of its blocks waits for an SM that an
-    // on-chip CTA occupies (a step lasts as long as its last block)
+    // on-chip CTA occupies (a step lasts as long as its last block), and
+    // on-chip requests that arrive during the step find room at once
     int oc = 0;
     for (int k = 0; k < sv->oc_slots; ++k) oc += sv->oc_req[k] ? 1 : 0;
     const int warps = oc > 0 ? sv->resident_warps / 4 * 3 : sv->resident_warps;
     lk.unlock();
     int st = ASYRK_OK;
-    cudaError_t e = cudaMemcpyAsync(sv->d, sv->h.data(), sv->max_slots * sizeof(SysDesc),
+    cudaError_t e = cudaMemcpyAsync(sv->d, sv->h.data(), hi * sizeof(SysDesc),
                                     cudaMemcpyHostToDevice, sv->s);
     if (e == cudaSuccess)
-        st = launch_engine_step(sv->d, sv->max_slots, chunks, sv->part, warps, sv->excl, true,
-                                sv->s);
+        st = launch_engine_step(sv->d, hi, chunks, sv->part, warps, sv->excl, true, sv->s);
     if (e == cudaSuccess && st == ASYRK_OK)
-        e = cudaMemcpyAsync(sv->h.data(), sv->d, sv->max_slots * sizeof(SysDesc),
-                            cudaMemcpyDeviceToHost, sv->s);
+        e = cudaMemcpyAsync(sv->h.data(), sv->d, hi * sizeof(SysDesc), cudaMemcpyDeviceToHost,
+                            sv->s);
     if (e == cudaSuccess && st == ASYRK_OK) e = cudaStreamSynchronize(sv->s);
     lk.lock();
     if (e != cudaSuccess) return cuda_fail(e, "server step", __FILE__, __LINE__);
@@ -571,7 +578,7 @@ static int engine_step(asyrk_server *sv, std::unique_lock<std::mutex> &lk, std::
     sv->iterations += 1;
     sv->launches += 5;
     done.clear();
-    for (int k = 0; k < sv->max_slots; ++k)
+    for (int k = 0; k < hi; ++k)
         if (sv->slot_req[k] && !sv->h[k].active) done.push_back(k);
     return ASYRK_OK;
 }
@@ -624,7 +631,20 @@ static void engine_loop(asyrk_server *sv)
     std::unique_lock<std::mutex> lk(sv->mu);
     std::vector<int> done;
     for (;;) {
-        // admission: FIFO into free slots while memory allows
+        // admission: FIFO into free slots while memory allows and while the
+        // warp demands of the requests in the step stay within admit_load x the
+        // resident warps.  Past that point another request would only split the
+        // warps further: every request in the step would run with fewer, more
+        // latency-bound workers and all of them would finish late, so the rest
+        // wait in the queue (one request is always admitted).
+        long long demand = 0;
+        int in_step = 0;
+        for (int k = 0; k < sv->max_slots; ++k)
+            if (sv->slot_req[k]) {
+                demand += sv->slot_req[k]->demand;
+                in_step += 1;
+            }
+        const double limit = sv->admit_load * (double)sv->resident_warps;
         for (int k = 0; k < sv->max_slots && !sv->queue.empty(); ++k) {
             if (sv->slot_req[k]) continue;
             Request *r = sv->queue.front();
@@ -634,13 +654,17 @@ static void engine_loop(asyrk_server *sv)
                 --k;
                 continue;
             }
+            if (in_step > 0 && sv->admit_load > 0.0 && (double)(demand + r->demand) > limit) break;
             if (!admit_locked(sv, r, k)) break;
             sv->queue.pop_front();
+            demand += r->demand;
+            in_step += 1;
         }
         int occupied = 0, oc = 0;
         for (int k = 0; k < sv->max_slots; ++k) occupied += sv->slot_req[k] ? 1 : 0;
         for (int k = 0; k < sv->oc_slots; ++k) oc += sv->oc_req[k] ? 1 : 0;
         if (occupied + oc > sv->max_active) sv->max_active = occupied + oc;
+        if (occupied > sv->max_active_shared) sv->max_active_shared = occupied;
         if (sv->stop) {
             fail_shared_locked(sv, sv->fatal != ASYRK_OK ? sv->fatal : ASYRK_ECANCELED);
             break;
@@ -727,6 +751,8 @@ extern "C" int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *
     if (o.row_exclusion < -1 || o.row_exclusion > 1)
         return set_error(ASYRK_EINVAL, "row_exclusion must be -1, 0 or 1");
     if (o.inner_tol < 0.0 || o.max_inner_sweeps < 0) return set_error(ASYRK_EINVAL, "bad inner solve limits");
+    if (o.reserved != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
+    if (!(o.admit_load == o.admit_load)) return set_error(ASYRK_EINVAL, "admit_load is NaN");
     asyrk_server *sv = new (std::nothrow) asyrk_server();
     if (!sv) return set_error(ASYRK_ENOMEM, "host allocation failed");
     auto fail = [&](int st) {
@@ -743,6 +769,7 @@ extern "C" int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *
     sv->excl = o.row_exclusion >= 0;
     if (o.inner_tol > 0.0) sv->inner_tol = o.inner_tol;
     if (o.max_inner_sweeps > 0) sv->max_inner = o.max_inner_sweeps;
+    if (o.admit_load != 0.0) sv->admit_load = o.admit_load > 0.0 ? o.admit_load : -1.0;
     cudaError_t e = cudaGetDevice(&sv->device);
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device);
@@ -849,6 +876,10 @@ extern "C" int asyrk_server_submit(asyrk_server *sv, asyrk_problem *p, const dou
             }
         }
     }
+    if (!r->onchip) {
+        const long long cw = (tau_cap_estimate(p->m, p->n) * engine_subwarp(p, false) + 31) / 32;
+        r->demand = cw < 1 ? 1 : cw > sv->resident_warps ? sv->resident_warps : cw;
+    }
     r->ticket = sv->next_ticket++;
     r->t_submit = now_s();
     (r->onchip ? sv->oc_queue : sv->queue).push_back(r);
@@ -921,6 +952,7 @@ extern "C" int asyrk_server_get_stats(asyrk_server *sv, asyrk_server_stats *st)
     st->arena_reserved = (int64_t)sv->arena->reserved();
     st->max_slots = sv->max_slots;
     st->max_active = (int32_t)sv->max_active;
+    st->max_active_shared = (int32_t)sv->max_active_shared;
     st->fatal = sv->fatal;
     return ASYRK_OK;
 }

@@ -202,3 +202,24 @@ def test_cancel_a_running_onchip_request(pool):
         st, _, info = sv.wait(t, systems[2].n, timeout_us=60_000_000)
         assert st == asyrk.ECANCELED and info.sweeps >= 1
         assert sv.stats()["onchip_completed"] == 1
+
+
+def test_admission_caps_the_warp_demand_of_the_shared_step(pool):
+    # the 65536 x 16384 system's Cor. 2 worker cap is ~1340 workers, ~335 warps;
+    # with admit_load 0.1 (a tenth of the resident warps) two of them exceed
+    # the limit, so the shared step runs them one after another; with no limit
+    # they run together; the results reach the tolerance either way
+    systems, probs = pool
+    s, p = systems[4], probs[4]
+    for load, one_at_a_time in ((0.1, True), (-1.0, False)):
+        with asyrk.Server(8 << 30, max_slots=8, onchip=False, admit_load=load) as sv:
+            ts = [sv.submit(p, x_true=s.x_true, tol=1e-6) for _ in range(4)]
+            for t in ts:
+                st, x, _ = sv.wait(t, s.n, timeout_us=60_000_000)
+                assert st == asyrk.OK and _err(x, s) <= 1e-6
+            stt = sv.stats()
+            assert stt["completed"] == 4 and stt["fatal"] == 0
+            if one_at_a_time:
+                assert stt["max_active_shared"] == 1
+            else:
+                assert stt["max_active_shared"] >= 2
