@@ -69,13 +69,19 @@ def parse_args():
                     help="shrink m and n by 2^scale (testing only; not a bench number)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain/refine, batched and served measurements")
-    ap.add_argument("--served-seconds", type=float, default=10.0,
+    ap.add_argument("--served-seconds", type=float, default=30.0,
                     help="length of the Poisson arrival window of the served measurement")
+    ap.add_argument("--served-seconds2", type=float, default=10.0,
+                    help="arrival window of the second, lower-rate served measurement")
+    ap.add_argument("--admit-load", type=float, default=0.0,
+                    help="server admission limit (warp demand / resident warps; 0: default)")
     ap.add_argument("--served-rate", type=float, default=2000.0, help="requests per second")
     ap.add_argument("--served-rate2", type=float, default=1000.0,
                     help="a second, lower offered rate (0: skip)")
     ap.add_argument("--batched-only", action="store_true",
                     help="profiling aid: run only the 256-system batched case, print its JSON")
+    ap.add_argument("--served-only", action="store_true",
+                    help="tuning aid: run only the served measurement(s), print their JSON")
     ap.add_argument("--batch-host-loop", action="store_true",
                     help="with --batched-only: host-driven engine loop (separate launches)")
     return ap.parse_args()
@@ -715,7 +721,7 @@ def extras_batched(asyrk, synth, torch, graph=True):
     return out
 
 
-def extras_served(asyrk, synth, torch, seconds, rate):
+def extras_served(asyrk, synth, torch, seconds, rate, admit_load=0.0):
     import threading
     pool = {"small_bf16": [], "small_f32": [], "large_bf16": [], "large_f32": []}
     xts = {}
@@ -749,7 +755,7 @@ def extras_served(asyrk, synth, torch, seconds, rate):
         p = pool[cls][int(rng.integers(len(pool[cls])))]
         reqs.append((t, p, tol, asyrk.MODE_REFINE if refine else asyrk.MODE_ASYNC, cls))
     tickets = [None] * len(reqs)
-    sv = asyrk.Server(120 << 30, max_slots=512)
+    sv = asyrk.Server(120 << 30, max_slots=512, admit_load=admit_load)
     # warm-up: one request of each class
     for cls in pool:
         p = pool[cls][0]
@@ -801,6 +807,7 @@ def extras_served(asyrk, synth, torch, seconds, rate):
                              "p99_ms": 1e3 * float(np.percentile(v, 99))}
                          for c, v in sorted(lat.items())},
            "engine_steps": stats["iterations"], "max_in_flight": stats["max_active"],
+           "max_in_shared_step": stats["max_active_shared"], "admit_load": admit_load,
            "solved_on_chip": stats["onchip_completed"]}
     # the plain single-system FP32 kernel, one request at a time, at 1e-6
     times = {}
@@ -901,24 +908,48 @@ def run_asyrk(args, dist):
         ops = 1 << 28
         st_, pms = asyrk.asyrk_probe(kind, s.n, ops)
         probe[name] = ops / (pms / 1e3) if st_ == asyrk.OK and pms > 0 else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                else "fallback 6.8 TB/s",
-                "kernel": "k_project<float,float,8> (one sweep per launch)",
-                "binding": "L2: ~64 random 4-byte gathers/red.adds per projection on the "
-                           "L2-resident x, and their latency (ncu: L2 tag requests ~73% of "
-                           "peak, DRAM ~8%, long-scoreboard stalls); DRAM traffic per launch "
-                           "is ~1.04x the algorithmic bytes",
-                "bytes_per_projection": BYTES_PER_PROJECTION,
-                "projections_per_launch": per_launch_proj,
-                "launch_ms": per_launch_s * 1e3,
-                "kernel_share_of_step": proj_ms / ms,
-                "l2": {"achieved_gather_red_pairs_per_s": 32 * per_launch_proj / per_launch_s,
-                       "probe": probe,
-                       "frac_of_probe_pairs": (32 * per_launch_proj / per_launch_s /
-                                               probe["gather_red_pairs_per_s"])
-                       if probe.get("gather_red_pairs_per_s") else None}}
+    # the bound of the row-projection kernel: min(HBM / 280 B, red-rate / 32,
+    # gather+red pair rate / 32) projections/s.  x (n FP32 = 4 MB) is L2-resident,
+    # so the binding resource is the L2 atomic rate: the line reports the kernel's
+    # red.add.f32 rate (32 per applied projection) against the probe's rate of
+    # random red.add.f32 on an array of x's size, measured now on this GPU, with
+    # the HBM fraction of the row stream beside it
+    reds_per_s = 32 * per_launch_proj / per_launch_s
+    red_peak = probe.get("red_f32_per_s")
+    pair_peak = probe.get("gather_red_pairs_per_s")
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+           if peak_kind == "measured" else "fallback 6.8 TB/s",
+           "bytes_per_projection": BYTES_PER_PROJECTION}
+    bounds = {"hbm_projections_per_s": peak * 1e9 / BYTES_PER_PROJECTION,
+              "l2_red_projections_per_s": red_peak / 32 if red_peak else None,
+              "l2_gather_red_projections_per_s": pair_peak / 32 if pair_peak else None}
+    l2_resident = 4 * s.n <= (64 << 20)
+    if l2_resident and red_peak:
+        roofline = {"bound": "l2_atomic", "achieved": reds_per_s / 1e9, "peak": red_peak / 1e9,
+                    "unit": "G red.add.f32/s", "frac": reds_per_s / red_peak,
+                    "peak_source": "measured in this run on this GPU: asyrk_probe "
+                                   "PROBE_RED_F32, 2^28 random red.add.f32 on an n-float array "
+                                   "(the size of x), 8 in flight per thread, CUDA events",
+                    "traffic": traffic, "hbm": hbm}
+    else:
+        roofline = dict(bound="hbm", traffic=traffic, **hbm)
+    roofline.update({
+        "kernel": "k_project<float,float,8> (one sweep per launch)",
+        "binding": "L2: ~64 random 4-byte gathers/red.adds per projection on the "
+                   "L2-resident x, and their latency (ncu: L2 tag requests ~75% of "
+                   "peak, DRAM ~9%, long-scoreboard stalls)",
+        "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + write.sum)",
+        "projections_per_launch": per_launch_proj,
+        "launch_ms": per_launch_s * 1e3,
+        "kernel_share_of_step": proj_ms / ms,
+        "bounds_projections_per_s": bounds,
+        "achieved_projections_per_s": per_launch_proj / per_launch_s,
+        "l2": {"achieved_red_f32_per_s": reds_per_s,
+               "achieved_gather_red_pairs_per_s": reds_per_s,
+               "probe": probe,
+               "frac_of_probe_red": reds_per_s / red_peak if red_peak else None,
+               "frac_of_probe_pairs": reds_per_s / pair_peak if pair_peak else None}})
     # the workload's gamma sweep {0.5, 1}: time to tol and sweeps for each
     gamma_sweep = None
     if dist.rank == 0 and not args.no_extras:
@@ -956,7 +987,7 @@ def run_asyrk(args, dist):
             best = ms_c if best is None else min(best, ms_c)
         h2d_gbs = h_col.numel() * h_col.element_size() / (best / 1e3) / 1e9
         del d_col
-    e2e_t, e2e_proj = 0.0, 0
+    e2e_t, e2e_proj, e2e_sweeps = 0.0, 0, 0
     split = {"create_s": 0.0, "solve_s": 0.0, "destroy_s": 0.0}
     for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):  # first round warms up
         torch.cuda.synchronize()
@@ -977,11 +1008,17 @@ def run_asyrk(args, dist):
         if k > 0:
             e2e_t += dt
             e2e_proj += info.projections - info.skipped
+            e2e_sweeps += info.sweeps
     e2e_t = dist.reduce(e2e_t, "max")
     e2e_proj = dist.reduce(e2e_proj, "sum")
-    h2d = (s.row_ptr.nbytes + s.col.nbytes + s.val_store.nbytes + s.b.nbytes + 8 * s.m
-           + 2 * 8 * s.n)  # CSR, b, alias table, x0, x*
-    d2h = 2 * 8 * s.m + 8 * s.n  # row weights and b back for the alias table, x
+    # what crosses the host link per step: asyrk_create copies the CSR arrays and
+    # b (the row records and the alias table are built on the GPU); the solve
+    # copies x0 and x* in and x out, and reads one 8-byte measure per check (a
+    # check after every sweep, plus the initial one) and a few status words
+    h2d = (s.row_ptr.nbytes + s.col.nbytes + s.val_store.nbytes + s.b.nbytes
+           + 2 * 8 * s.n)
+    checks = e2e_sweeps / max(1, args.e2e_steps) + 1
+    d2h = 8 * s.n + 8 * checks + 64
     e2e = None if args.e2e_steps <= 0 else {"value": e2e_proj / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h),
            "what": "asyrk_create from pinned host CSR + asyrk_solve (host x0 -> host x) + destroy",
@@ -1020,10 +1057,11 @@ def run_asyrk(args, dist):
                   "tau_threshold": guarded(extras_tau_threshold, asyrk, synth),
                   "batched": guarded(extras_batched, asyrk, synth, torch),
                   "served": guarded(extras_served, asyrk, synth, torch, args.served_seconds,
-                                    args.served_rate)}
+                                    args.served_rate, args.admit_load)}
         if args.served_rate2 > 0:
             extras["served_lower_rate"] = guarded(extras_served, asyrk, synth, torch,
-                                                  args.served_seconds, args.served_rate2)
+                                                  args.served_seconds2, args.served_rate2,
+                                                  args.admit_load)
 
     if dist.rank == 0:
         cfg = workload_config(s, args)
@@ -1048,6 +1086,18 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.served_only:
+            import torch
+            from paper_1401_4780_gb300 import asyrk, synth
+            torch.cuda.set_device(dist.local_rank)
+            asyrk.load()
+            out = {"served": extras_served(asyrk, synth, torch, args.served_seconds,
+                                           args.served_rate, args.admit_load)}
+            if args.served_rate2 > 0:
+                out["served_lower_rate"] = extras_served(asyrk, synth, torch,
+                                                         args.served_seconds2,
+                                                         args.served_rate2, args.admit_load)
+            print(json.dumps(out), flush=True)
         elif args.batched_only:
             import torch
             from paper_1401_4780_gb300 import asyrk, synth
