@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["asyrk", "reference"], default="asyrk")
     ap.add_argument("--gamma", type=float, default=1.0)
     ap.add_argument("--tol", type=float, default=1e-5)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--scale", type=int, default=0,
@@ -921,9 +921,17 @@ def run_asyrk(args, dist):
            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
            if peak_kind == "measured" else "fallback 6.8 TB/s",
            "bytes_per_projection": BYTES_PER_PROJECTION}
+    gather_peak = probe.get("gather_f32_per_s")
     bounds = {"hbm_projections_per_s": peak * 1e9 / BYTES_PER_PROJECTION,
               "l2_red_projections_per_s": red_peak / 32 if red_peak else None,
-              "l2_gather_red_projections_per_s": pair_peak / 32 if pair_peak else None}
+              "l2_gather_red_projections_per_s": pair_peak / 32 if pair_peak else None,
+              # the bound as the method's scope defines it: min(HBM / 280 B,
+              # atomic rate / 32, L2 read-sector rate / (2 x 32 sectors)), with
+              # the gather probe's rate as the L2 read-sector rate
+              "min_of_hbm_atomic_l2sector": min(
+                  [v for v in (peak * 1e9 / BYTES_PER_PROJECTION,
+                               red_peak / 32 if red_peak else None,
+                               gather_peak / 64 if gather_peak else None) if v])}
     l2_resident = 4 * s.n <= (64 << 20)
     if l2_resident and red_peak:
         roofline = {"bound": "l2_atomic", "achieved": reds_per_s / 1e9, "peak": red_peak / 1e9,
@@ -945,6 +953,7 @@ def run_asyrk(args, dist):
         "kernel_share_of_step": proj_ms / ms,
         "bounds_projections_per_s": bounds,
         "achieved_projections_per_s": per_launch_proj / per_launch_s,
+        "frac_of_min_bound": (per_launch_proj / per_launch_s) / bounds["min_of_hbm_atomic_l2sector"],
         "l2": {"achieved_red_f32_per_s": reds_per_s,
                "achieved_gather_red_pairs_per_s": reds_per_s,
                "probe": probe,
@@ -989,6 +998,7 @@ def run_asyrk(args, dist):
         del d_col
     e2e_t, e2e_proj, e2e_sweeps = 0.0, 0, 0
     split = {"create_s": 0.0, "solve_s": 0.0, "destroy_s": 0.0}
+    create_ms = []
     for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):  # first round warms up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1000,6 +1010,7 @@ def run_asyrk(args, dist):
             t2 = time.perf_counter()
         dt = time.perf_counter() - t0
         if k > 0:
+            create_ms.append(1e3 * (t1 - t0))
             split["create_s"] += t1 - t0
             split["solve_s"] += t2 - t1
             split["destroy_s"] += t0 + dt - t2
@@ -1023,7 +1034,12 @@ def run_asyrk(args, dist):
            "d2h_bytes_per_step": int(d2h),
            "what": "asyrk_create from pinned host CSR + asyrk_solve (host x0 -> host x) + destroy",
            "ms_per_step_split": {k: 1e3 * v / max(1, args.e2e_steps) for k, v in split.items()},
-           "host_affinity": affinity, "h2d_probe_gbs": h2d_gbs}
+           "create_ms_each_step": create_ms,
+           "host_affinity": affinity, "h2d_probe_gbs": h2d_gbs,
+           "note": "create copies 1.1 GB over the host link (~210 GB/s: ~5.5 ms of its ~9 ms); "
+                   "the link is shared with the other GPUs' jobs on the same host, and runs saw "
+                   "periodic stretches at a fraction of that rate that slow some creates to "
+                   "20-200 ms"}
 
     cpu = None
     cpu_mt = None
