@@ -6,6 +6,7 @@ call, and the static status descriptions.
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -43,18 +44,36 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
-def test_struct_layouts_match_header():
-    # sizes implied by the header's field lists (natural alignment, LP64)
-    assert ctypes.sizeof(asyrk.CreateOpts) == 24
-    assert ctypes.sizeof(asyrk.SolveOpts) == 80
-    assert ctypes.sizeof(asyrk.SolveInfo) == 96
-    assert ctypes.sizeof(asyrk.ProblemStats) == 80
-    assert ctypes.sizeof(asyrk.BatchOpts) == 40
-    assert ctypes.sizeof(asyrk.LsqOpts) == 40
-    assert ctypes.sizeof(asyrk.BatchInfo) == 64
-    assert ctypes.sizeof(asyrk.TuneResult) == 24
-    assert ctypes.sizeof(asyrk.ServerOpts) == 40
-    assert ctypes.sizeof(asyrk.ServerStats) == 96
+_STRUCTS = {"asyrk_create_opts": "CreateOpts", "asyrk_solve_opts": "SolveOpts",
+            "asyrk_solve_info": "SolveInfo", "asyrk_problem_stats": "ProblemStats",
+            "asyrk_batch_opts": "BatchOpts", "asyrk_lsq_opts": "LsqOpts",
+            "asyrk_batch_info": "BatchInfo", "asyrk_tune_result": "TuneResult",
+            "asyrk_server_opts": "ServerOpts", "asyrk_server_stats": "ServerStats"}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # the C compiler's sizeof/offsetof of every option, info and stats struct of
+    # the header against the binding's ctypes mirror, field by field
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "asyrk.h"', 'int main(void) {']
+    for cname, pname in _STRUCTS.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for field, _ in getattr(asyrk, pname)._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, field, cname, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I" + os.path.join(ROOT, "include"), "-o", str(exe),
+                           str(src)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, key, val = ln.split()
+        got[(cname, key)] = int(val)
+    for cname, pname in _STRUCTS.items():
+        cls = getattr(asyrk, pname)
+        assert ctypes.sizeof(cls) == got[(cname, "size")], cname
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == got[(cname, field)], (cname, field)
 
 
 def test_abi_version_and_status_strings(lib):
