@@ -954,6 +954,10 @@ def run_asyrk(args, dist):
         "bounds_projections_per_s": bounds,
         "achieved_projections_per_s": per_launch_proj / per_launch_s,
         "frac_of_min_bound": (per_launch_proj / per_launch_s) / bounds["min_of_hbm_atomic_l2sector"],
+        # the L2 pipe's time per second if gathers and red.adds take turns in it:
+        # reds at the red-only rate plus gathers at the gather-only rate
+        "l2_op_time_frac": (reds_per_s / red_peak + reds_per_s / gather_peak)
+        if red_peak and gather_peak else None,
         "l2": {"achieved_red_f32_per_s": reds_per_s,
                "achieved_gather_red_pairs_per_s": reds_per_s,
                "probe": probe,

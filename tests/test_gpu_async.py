@@ -121,8 +121,10 @@ def test_large_async_workload_full_size():
     with asyrk.Problem.from_system(s) as p:
         st_ = p.stats()
         assert st_["m"] == 1 << 22 and st_["nnz"] == 32 << 22 and st_["uniform"] == 0
-        # the sampler on sampled positions of the full-size table
+        # the sampler on sampled positions of the full-size table; F of the
+        # 4,194,304 row weights is the same correctly rounded sum on both sides
         samp = oracle.Sampler(s.m, s.row_ptr, s.val64)
+        assert st_["frob2"] == samp.F
         for j0 in (0, 123_456_789, 2**32 - 3):
             np.testing.assert_array_equal(
                 p.draw_rows(j0, 20000), oracle.draw_rows(seed, 0, j0, 20000, samp.thr, samp.alias,
