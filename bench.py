@@ -711,6 +711,7 @@ def extras_batched(asyrk, synth, torch, graph=True):
            "max_rel_err_host": max(errs), "sweeps_median": float(np.median(sweeps)),
            "sweeps_max": int(max(sweeps)), "kernel_launches": bi.kernel_launches,
            "resident_warps": bi.resident_warps, "autotuned_by_row_length_class": tuned,
+           "global_engine_sms": bi.global_sms,
            "plain_fp32_one_at_a_time": {"wall_ms": 1e3 * t_plain, "converged": ok_plain,
                                         "projections_per_s": proj_plain / t_plain},
            "speedup_vs_one_at_a_time": t_plain / bi.seconds,

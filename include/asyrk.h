@@ -314,6 +314,10 @@ typedef struct asyrk_batch_opts {
     int32_t cluster_max;    /* ONCHIP: CTAs per cluster at most, 1, 2, 4 or 8 (0: 4) */
     int32_t workers;        /* ONCHIP: workers per member at most (0: the Cor. 2
                                estimate; 1: one worker, projections strictly in order) */
+    int32_t partition;      /* both engines at once, graph form: >= 0 splits the SMs
+                               between them, each engine on its own SMs, where the
+                               driver offers SM partitions (default); -1: both
+                               engines share every SM                               */
 } asyrk_batch_opts;
 
 typedef struct asyrk_batch_info {
@@ -328,6 +332,9 @@ typedef struct asyrk_batch_info {
     int32_t graph;            /* 1: the loop ran as one graph launch               */
     int32_t engine;           /* engines that ran: GLOBAL (1), ONCHIP (2), both (3) */
     int32_t onchip_members;   /* members the on-chip engine solved                 */
+    int32_t global_sms;       /* SMs of the global engine when the SMs were split
+                                 between the engines, else 0                        */
+    int32_t reserved;
 } asyrk_batch_info;
 
 /* Group `count` problems (FP32 or BF16 values, all on the current device, each

@@ -185,7 +185,8 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("graph", ctypes.c_int32),
                 ("row_exclusion", ctypes.c_int32), ("sampling", ctypes.c_int32),
                 ("update", ctypes.c_int32), ("engine", ctypes.c_int32),
-                ("cluster_max", ctypes.c_int32), ("workers", ctypes.c_int32)]
+                ("cluster_max", ctypes.c_int32), ("workers", ctypes.c_int32),
+                ("partition", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -194,7 +195,8 @@ class BatchInfo(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("device_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("resident_warps", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("engine", ctypes.c_int32),
-                ("onchip_members", ctypes.c_int32)]
+                ("onchip_members", ctypes.c_int32), ("global_sms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -361,12 +363,12 @@ def _ptr_array(items):
 
 def asyrk_batch_create(handles, stream=None, graph=True, row_exclusion=0,
                        sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW, engine=0, cluster_max=0,
-                       workers=0):
+                       workers=0, partition=True):
     b = ctypes.c_void_p()
     hs = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
     o = BatchOpts(stream=_stream(stream), graph=0 if graph else -1, row_exclusion=row_exclusion,
                   sampling=sampling, update=update, engine=engine, cluster_max=cluster_max,
-                  workers=workers)
+                  workers=workers, partition=0 if partition else -1)
     st = load().asyrk_batch_create(ctypes.byref(b), hs, len(handles), ctypes.byref(o))
     return st, b
 
@@ -591,16 +593,18 @@ class Batch:
     engine: ENGINE_AUTO (members that fit a CTA's shared memory on-chip, the rest in
     the global-iterate engine, both at once), ENGINE_GLOBAL or ENGINE_ONCHIP (every
     member on-chip, else EINVAL); cluster_max: CTAs per on-chip cluster at most
-    (0: one); workers: on-chip workers per member at most (0: the Cor. 2 estimate).
+    (0: one); workers: on-chip workers per member at most (0: the Cor. 2 estimate);
+    partition: with both engines at once, split the SMs between them (False: share).
     """
 
     def __init__(self, problems, stream=None, graph=True, row_exclusion=0,
                  sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW, engine=0, cluster_max=0,
-                 workers=0):
+                 workers=0, partition=True):
         self.problems = list(problems)
         st, b = asyrk_batch_create([p.h for p in self.problems], stream=stream, graph=graph,
                                    row_exclusion=row_exclusion, sampling=sampling, update=update,
-                                   engine=engine, cluster_max=cluster_max, workers=workers)
+                                   engine=engine, cluster_max=cluster_max, workers=workers,
+                                   partition=partition)
         if st != OK:
             raise AsyrkError(st, "asyrk_batch_create")
         self.b = b

@@ -13,8 +13,11 @@
 //     iteration (plan, project, check, cond), stopped on the device when no
 //     slot is active or after the iteration bound.
 // The largest members that fit still go to the global engine while that
-// shortens the estimated batch time (plan_members).  asyrk_batch_solve: copy
-// inputs, launch both graphs on two streams at once, copy results.
+// shortens the estimated batch time (plan_members).  When both engines run,
+// the SMs are split between them (partition.cuh): the on-chip engine gets
+// enough SMs for its members' thread-time within 1/2.5 of its longest member's
+// solve, the global engine the rest, each on its own stream.  asyrk_batch_solve:
+// copy inputs, launch both graphs at once, copy results.
 #include <math.h>
 #include <string.h>
 
@@ -26,6 +29,7 @@
 
 #include "batch.cuh"
 #include "cluster.cuh"
+#include "partition.cuh"
 
 struct asyrk_batch {
     int count = 0;
@@ -64,6 +68,10 @@ struct asyrk_batch {
     cudaGraphExec_t exec_on = nullptr;
     cudaStream_t side = nullptr;         // the global engine's stream when both run
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // both engines at once: the SMs split between them (stream 0 global, 1 on-chip)
+    asyrk::SmPartition split;
+    int resident_warps_glob = 0;         // the global engine's warps on its SMs
+    cudaEvent_t ev_on_join = nullptr;
 };
 
 using namespace asyrk;
@@ -78,6 +86,8 @@ static void batch_free(asyrk_batch *b)
     if (b->side) cudaStreamDestroy(b->side);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->ev_on_join) cudaEventDestroy(b->ev_on_join);
+    sm_partition_destroy(&b->split);
     cudaFree(b->d);
     cudaFree(b->x);
     cudaFree(b->x64);
@@ -120,7 +130,8 @@ static int build_graph(asyrk_batch *b)
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     ASYRK_CK(cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeRelaxed));
-    int st = launch_batch_iteration(b->d, b->count, b->total_chunks, b->part, b->resident_warps,
+    const int warps = b->resident_warps_glob > 0 ? b->resident_warps_glob : b->resident_warps;
+    int st = launch_batch_iteration(b->d, b->count, b->total_chunks, b->part, warps,
                                     b->excl, b->d_active, b->d_iter, true,
                                     (unsigned long long)handle, b->cap_stream);
     cudaGraph_t captured = nullptr;
@@ -264,6 +275,7 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
         o.cluster_max != 8)
         return set_error(ASYRK_EINVAL, "cluster_max must be 0, 1, 2, 4 or 8");
     if (o.workers < 0) return set_error(ASYRK_EINVAL, "workers < 0");
+    if (o.partition < -1) return set_error(ASYRK_EINVAL, "partition must be >= -1");
     std::set<asyrk_problem *> seen;
     int dev = -1;
     ASYRK_CK(cudaGetDevice(&dev));
@@ -313,7 +325,11 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
         D.n = (unsigned)p->n;
         D.dtype = p->dtype;
         D.uniform = p->uniform;
-        D.work = (double)p->nnz;
+        // the plan splits the warps in proportion to this: a sweep's time
+        // grows with the stored entries and, by a fixed latency per
+        // projection, with the rows (measured on the 256-system workload:
+        // 89-90 ms with the global engine alone against 92 ms for entries only)
+        D.work = (double)p->nnz + 16.0 * (double)p->m;
         D.key = make_uint2((unsigned)p->seed, (unsigned)(p->seed >> 32));
         D.rec = p->rec;
         D.col = p->col;
@@ -394,6 +410,28 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
             e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
         if (e != cudaSuccess) return fail(cuda_fail(e, "on-chip batch set-up", __FILE__, __LINE__));
         if (b->graph && (st = build_onchip_graph(b)) != ASYRK_OK) return fail(st);
+    }
+    if (b->n_glob > 0 && b->n_on > 0 && b->graph && o.partition >= 0) {
+        // SMs for the on-chip engine: its members' thread-time per sweep within
+        // 1/2.5 of its longest member's sweep (one CTA each; clusters need
+        // co-scheduled SMs and keep the whole GPU)
+        double longest = 0.0, area = 0.0;
+        bool single = true;
+        for (int k = 0; k < count; ++k) {
+            if (!b->on[k]) continue;
+            const double t = onchip_sweep_seconds(b, k);
+            longest = std::max(longest, t);
+            area += t * (double)b->shapes[k].threads;
+            single = single && b->shapes[k].C == 1;
+        }
+        int on_sms = (int)ceil(2.5 * area / (THREADS_PER_SM * (longest > 0.0 ? longest : 1.0)));
+        on_sms = std::max(8, std::min(on_sms, sms - 8));
+        if (single && sm_partition_create(dev, sms - on_sms, &b->split)) {
+            b->resident_warps_glob =
+                std::max(8, (int)((long long)b->resident_warps * b->split.sms[0] / sms));
+            if (cudaEventCreateWithFlags(&b->ev_on_join, cudaEventDisableTiming) != cudaSuccess)
+                return fail(cuda_fail(cudaGetLastError(), "batch event", __FILE__, __LINE__));
+        }
     }
     if (b->n_glob > 0 && b->graph && (st = build_graph(b)) != ASYRK_OK) return fail(st);
     *out = b;
@@ -483,7 +521,9 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
     ASYRK_CK(cudaEventRecord(b->ev[0], s));
     // the global engine's members: on a second stream when the on-chip engine
     // runs at the same time (graph form), else on the batch's stream
-    cudaStream_t gs = (b->n_on > 0 && b->n_glob > 0 && b->graph) ? b->side : s;
+    const bool both = b->n_on > 0 && b->n_glob > 0 && b->graph;
+    cudaStream_t gs = both ? (b->split.stream[0] ? b->split.stream[0] : b->side) : s;
+    cudaStream_t os = (both && b->split.stream[1]) ? b->split.stream[1] : s;
     if (b->n_glob > 0) {
         if (gs != s) {
             ASYRK_CK(cudaEventRecord(b->ev_fork, s));
@@ -510,14 +550,22 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
         if (gs != s) ASYRK_CK(cudaEventRecord(b->ev_join, gs));
     }
     if (b->n_on > 0) {
+        if (os != s) {
+            ASYRK_CK(cudaEventRecord(b->ev_fork, s));
+            ASYRK_CK(cudaStreamWaitEvent(os, b->ev_fork, 0));
+        }
         if (b->graph) {
-            ASYRK_CK(cudaGraphLaunch(b->exec_on, s));
+            ASYRK_CK(cudaGraphLaunch(b->exec_on, os));
         } else {
             for (int k : b->order)
                 if ((st = cluster_launch(b->probs[k]->dtype, b->shapes[k], b->jobs, k, s)) != ASYRK_OK)
                     return st;
         }
         launches += b->n_on;
+        if (os != s) {
+            ASYRK_CK(cudaEventRecord(b->ev_on_join, os));
+            ASYRK_CK(cudaStreamWaitEvent(s, b->ev_on_join, 0));
+        }
         ASYRK_CK(cudaMemcpyAsync(b->hj.data(), b->jobs, b->count * sizeof(ClusterJob),
                                  cudaMemcpyDeviceToHost, s));
     }
@@ -590,6 +638,7 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
         binfo->graph = b->graph ? 1 : 0;
         binfo->engine = (b->n_glob > 0 ? ASYRK_ENGINE_GLOBAL : 0) | (b->n_on > 0 ? ASYRK_ENGINE_ONCHIP : 0);
         binfo->onchip_members = b->n_on;
+        binfo->global_sms = b->split.sms[0];
     }
     return worst;
 }

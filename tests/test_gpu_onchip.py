@@ -196,14 +196,17 @@ def test_engine_selection():
             assert bi.engine == asyrk.ENGINE_GLOBAL
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_hybrid_batch_reaches_tolerance(graph):
-    # two members exceed a CTA's shared memory (x alone 256 KiB): global engine
+@pytest.mark.parametrize("graph,partition", [(True, True), (True, False), (False, True)])
+def test_hybrid_batch_reaches_tolerance(graph, partition):
+    # two members exceed a CTA's shared memory (x alone 256 KiB): global engine.
+    # Graph-launched, the two engines run at once, by default each on its own
+    # share of the SMs (green contexts); without the split they share every SM;
+    # the host-driven loop runs the engines one after the other, unsplit
     systems = _systems()[:5] + [synth.make_system(4 * 65536, 65536, 12, 50 + k, row_norms="unit",
                                                   value_dtype="f32") for k in range(2)]
     probs = [asyrk.Problem.from_system(s) for s in systems]
     try:
-        with asyrk.Batch(probs, graph=graph) as b:
+        with asyrk.Batch(probs, graph=graph, partition=partition) as b:
             xs = [np.zeros(s.n) for s in systems]
             st, infos, bi = b.solve(xs, tols=[1e-6] * len(systems), max_sweeps=400,
                                     x_trues=[s.x_true for s in systems])
@@ -211,6 +214,12 @@ def test_hybrid_batch_reaches_tolerance(graph):
             assert bi.engine == asyrk.ENGINE_ONCHIP | asyrk.ENGINE_GLOBAL
             assert 1 <= bi.onchip_members <= 5 and bi.converged == len(systems)
             assert bi.iterations == max(i.sweeps for i in infos)
+            if graph and partition:
+                import torch
+                sms = torch.cuda.get_device_properties(0).multi_processor_count
+                assert 8 <= bi.global_sms <= sms - 8
+            else:
+                assert bi.global_sms == 0
         for s, x, info, p in zip(systems, xs, infos, probs):
             assert _err(x, s) <= 1e-6 and abs(info.rel_err - _err(x, s)) <= 1e-3 * _err(x, s)
             assert info.rel_res < 1e-5
