@@ -75,6 +75,8 @@ def parse_args():
                     help="arrival window of the second, lower-rate served measurement")
     ap.add_argument("--admit-load", type=float, default=0.0,
                     help="server admission limit (warp demand / resident warps; 0: default)")
+    ap.add_argument("--server-partition", type=int, default=0,
+                    help="server: SMs of the on-chip requests (0: default, -1: no split)")
     ap.add_argument("--served-rate", type=float, default=2000.0, help="requests per second")
     ap.add_argument("--served-rate2", type=float, default=1000.0,
                     help="a second, lower offered rate (0: skip)")
@@ -722,7 +724,7 @@ def extras_batched(asyrk, synth, torch, graph=True):
     return out
 
 
-def extras_served(asyrk, synth, torch, seconds, rate, admit_load=0.0):
+def extras_served(asyrk, synth, torch, seconds, rate, admit_load=0.0, partition=0):
     import threading
     pool = {"small_bf16": [], "small_f32": [], "large_bf16": [], "large_f32": []}
     xts = {}
@@ -756,7 +758,7 @@ def extras_served(asyrk, synth, torch, seconds, rate, admit_load=0.0):
         p = pool[cls][int(rng.integers(len(pool[cls])))]
         reqs.append((t, p, tol, asyrk.MODE_REFINE if refine else asyrk.MODE_ASYNC, cls))
     tickets = [None] * len(reqs)
-    sv = asyrk.Server(120 << 30, max_slots=512, admit_load=admit_load)
+    sv = asyrk.Server(120 << 30, max_slots=512, admit_load=admit_load, partition=partition)
     # warm-up: one request of each class
     for cls in pool:
         p = pool[cls][0]
@@ -809,6 +811,7 @@ def extras_served(asyrk, synth, torch, seconds, rate, admit_load=0.0):
                          for c, v in sorted(lat.items())},
            "engine_steps": stats["iterations"], "max_in_flight": stats["max_active"],
            "max_in_shared_step": stats["max_active_shared"], "admit_load": admit_load,
+           "sm_split": {"shared_step": stats["step_sms"], "on_chip": stats["onchip_sms"]},
            "solved_on_chip": stats["onchip_completed"]}
     # the plain single-system FP32 kernel, one request at a time, at 1e-6
     times = {}
@@ -1113,11 +1116,13 @@ def main():
             torch.cuda.set_device(dist.local_rank)
             asyrk.load()
             out = {"served": extras_served(asyrk, synth, torch, args.served_seconds,
-                                           args.served_rate, args.admit_load)}
+                                           args.served_rate, args.admit_load,
+                                           args.server_partition)}
             if args.served_rate2 > 0:
                 out["served_lower_rate"] = extras_served(asyrk, synth, torch,
                                                          args.served_seconds2,
-                                                         args.served_rate2, args.admit_load)
+                                                         args.served_rate2, args.admit_load,
+                                                         args.server_partition)
             print(json.dumps(out), flush=True)
         elif args.batched_only:
             import torch

@@ -383,7 +383,13 @@ typedef struct asyrk_server_opts {
     int64_t max_inner_sweeps;  /* REFINE inner sweeps per outer step at most (0: 60) */
     int32_t onchip;            /* >= 0: requests whose problem fits a CTA's shared
                                   memory are solved on-chip (default); -1: never     */
-    int32_t reserved;          /* must be 0                                          */
+    int32_t partition;         /* with on-chip requests: the shared step and the
+                                  on-chip requests on disjoint SMs, the on-chip ones
+                                  on this many (0: 16; rounded up to the driver's
+                                  granularity) where the driver offers SM partitions;
+                                  -1: they share every SM (the step then takes three
+                                  quarters of the resident warps while on-chip
+                                  requests run)                                      */
     double admit_load;         /* shared-step admission: queued requests are admitted
                                   in arrival order while the warp demands of the
                                   requests in the step (each its Cor. 2 worker cap
@@ -405,6 +411,9 @@ typedef struct asyrk_server_stats {
     int32_t fatal;             /* first hard error of the engine, or OK              */
     int32_t max_active_shared; /* most requests in the shared engine step at once    */
     int64_t onchip_completed;  /* requests solved on-chip so far                     */
+    int32_t step_sms;          /* SMs of the shared step when split from the on-chip
+                                  requests' SMs, else 0                              */
+    int32_t onchip_sms;        /* SMs of the on-chip requests when split, else 0     */
 } asyrk_server_stats;
 
 /* Start a server on the current device.  Errors: EINVAL, ENOMEM, ECUDA. */

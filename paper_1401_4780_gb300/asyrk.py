@@ -206,7 +206,7 @@ class ServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("row_exclusion", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("max_inner_sweeps", ctypes.c_int64), ("onchip", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("admit_load", ctypes.c_double)]
+                ("partition", ctypes.c_int32), ("admit_load", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -216,7 +216,8 @@ class ServerStats(ctypes.Structure):
                 ("mem_used", ctypes.c_int64), ("mem_budget", ctypes.c_int64),
                 ("arena_reserved", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("max_active", ctypes.c_int32), ("fatal", ctypes.c_int32),
-                ("max_active_shared", ctypes.c_int32), ("onchip_completed", ctypes.c_int64)]
+                ("max_active_shared", ctypes.c_int32), ("onchip_completed", ctypes.c_int64),
+                ("step_sms", ctypes.c_int32), ("onchip_sms", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -393,12 +394,12 @@ def asyrk_batch_destroy(b):
 
 
 def asyrk_server_create(mem_budget_bytes, max_slots=0, row_exclusion=0, inner_tol=0.0,
-                        max_inner_sweeps=0, onchip=True, admit_load=0.0):
+                        max_inner_sweeps=0, onchip=True, admit_load=0.0, partition=0):
     h = ctypes.c_void_p()
     o = ServerOpts(mem_budget_bytes=int(mem_budget_bytes), max_slots=max_slots,
                    row_exclusion=row_exclusion, inner_tol=inner_tol,
                    max_inner_sweeps=max_inner_sweeps, onchip=0 if onchip else -1,
-                   admit_load=float(admit_load))
+                   admit_load=float(admit_load), partition=int(partition))
     st = load().asyrk_server_create(ctypes.byref(h), ctypes.byref(o))
     return st, h
 
@@ -643,12 +644,14 @@ class Server:
     admit_load: the shared step admits queued requests in arrival order while the
     warp demands of those in the step add up to at most admit_load x the resident
     warps (0: 1.0; < 0: no limit).
+    partition: SMs for the on-chip requests, the shared step on the others (0: 16;
+    -1: no split, both on every SM).
     """
 
     def __init__(self, mem_budget_bytes, max_slots=0, row_exclusion=0, inner_tol=0.0,
-                 max_inner_sweeps=0, onchip=True, admit_load=0.0):
+                 max_inner_sweeps=0, onchip=True, admit_load=0.0, partition=0):
         st, h = asyrk_server_create(mem_budget_bytes, max_slots, row_exclusion, inner_tol,
-                                    max_inner_sweeps, onchip, admit_load)
+                                    max_inner_sweeps, onchip, admit_load, partition)
         if st != OK:
             raise AsyrkError(st, "asyrk_server_create")
         self.h = h

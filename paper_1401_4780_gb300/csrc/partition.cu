@@ -43,6 +43,20 @@ void sm_partition_destroy(SmPartition *p)
     *p = SmPartition();
 }
 
+bool sm_partition_add_stream(const SmPartition &p, int g, cudaStream_t *s)
+{
+    *s = nullptr;
+    auto screate = (GreenCtxStreamCreateFn)entry("cuGreenCtxStreamCreate");
+    if (!screate || g < 0 || g > 1 || !p.ctx[g]) return false;
+    CUstream cs = nullptr;
+    if (screate(&cs, (CUgreenCtx)p.ctx[g], CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    *s = (cudaStream_t)cs;
+    return true;
+}
+
 bool sm_partition_create(int dev, int first, SmPartition *out)
 {
     *out = SmPartition();

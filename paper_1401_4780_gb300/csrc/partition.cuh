@@ -19,6 +19,9 @@ struct SmPartition {
 // false, holding nothing, when the driver offers no such split (then the
 // caller runs without one); errors of the driver are cleared.
 bool sm_partition_create(int dev, int first, SmPartition *out);
+// Another non-blocking stream in group g (the caller destroys it before the
+// partition); false when the driver refuses.
+bool sm_partition_add_stream(const SmPartition &p, int g, cudaStream_t *s);
 void sm_partition_destroy(SmPartition *p);
 
 }  // namespace asyrk

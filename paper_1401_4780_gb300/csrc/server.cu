@@ -36,6 +36,7 @@
 
 #include "batch.cuh"
 #include "cluster.cuh"
+#include "partition.cuh"
 
 namespace asyrk {
 
@@ -168,6 +169,10 @@ struct asyrk_server {
     int64_t max_inner = 60;
     double admit_load = 1.0;   // <= 0: admission bounded by slots and memory only
     int max_active_shared = 0;
+    // the shared step (group 0, stream s) and the on-chip requests (group 1) on
+    // disjoint SMs, when split
+    SmPartition split;
+    int step_warps = 0;        // the step's resident warps on its SMs (split only)
     cudaStream_t s = nullptr;
     SysDesc *d = nullptr;
     std::vector<SysDesc> h;
@@ -561,7 +566,9 @@ static int engine_step(asyrk_server *sv, std::unique_lock<std::mutex> &lk, std::
     // on-chip requests that arrive during the step find room at once
     int oc = 0;
     for (int k = 0; k < sv->oc_slots; ++k) oc += sv->oc_req[k] ? 1 : 0;
-    const int warps = oc > 0 ? sv->resident_warps / 4 * 3 : sv->resident_warps;
+    const int warps = sv->step_warps > 0 ? sv->step_warps
+                      : oc > 0           ? sv->resident_warps / 4 * 3
+                                         : sv->resident_warps;
     lk.unlock();
     int st = ASYRK_OK;
     cudaError_t e = cudaMemcpyAsync(sv->d, sv->h.data(), hi * sizeof(SysDesc),
@@ -751,13 +758,14 @@ extern "C" int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *
     if (o.row_exclusion < -1 || o.row_exclusion > 1)
         return set_error(ASYRK_EINVAL, "row_exclusion must be -1, 0 or 1");
     if (o.inner_tol < 0.0 || o.max_inner_sweeps < 0) return set_error(ASYRK_EINVAL, "bad inner solve limits");
-    if (o.reserved != 0) return set_error(ASYRK_EINVAL, "reserved option field must be 0");
+    if (o.partition < -1) return set_error(ASYRK_EINVAL, "partition must be >= -1");
     if (!(o.admit_load == o.admit_load)) return set_error(ASYRK_EINVAL, "admit_load is NaN");
     asyrk_server *sv = new (std::nothrow) asyrk_server();
     if (!sv) return set_error(ASYRK_ENOMEM, "host allocation failed");
     auto fail = [&](int st) {
-        if (sv->s) cudaStreamDestroy(sv->s);
+        if (sv->s && sv->s != sv->split.stream[0]) cudaStreamDestroy(sv->s);
         for (cudaStream_t x : sv->oc_stream) cudaStreamDestroy(x);
+        sm_partition_destroy(&sv->split);
         for (cudaEvent_t x : sv->oc_ev) cudaEventDestroy(x);
         cudaFree(sv->oc_jobs);
         cudaFree(sv->d);
@@ -791,13 +799,28 @@ extern "C" int asyrk_server_create(asyrk_server **out, const asyrk_server_opts *
     sv->arena = new (std::nothrow) Arena(sv->budget);
     if (!sv->arena) return fail(set_error(ASYRK_ENOMEM, "host allocation failed"));
     e = cudaMalloc((void **)&sv->d, sv->max_slots * sizeof(SysDesc));
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->s, cudaStreamNonBlocking);
+    // on-chip requests on a few SMs of their own, the shared step on the rest:
+    // the step's blocks then never wait for SMs the on-chip CTAs hold, and the
+    // on-chip requests never wait for the step's blocks
+    if (e == cudaSuccess && sv->oc_slots > 0 && o.partition >= 0) {
+        const int oc_sms = o.partition > 0 ? o.partition : 16;
+        if (oc_sms < sms && sm_partition_create(sv->device, sms - oc_sms, &sv->split)) {
+            sv->s = sv->split.stream[0];
+            sv->step_warps = (int)((long long)sv->resident_warps * sv->split.sms[0] / sms);
+            if (sv->step_warps < 8) sv->step_warps = 8;
+        }
+    }
+    if (e == cudaSuccess && !sv->s) e = cudaStreamCreateWithFlags(&sv->s, cudaStreamNonBlocking);
     if (e == cudaSuccess && sv->oc_slots > 0)
         e = cudaMalloc((void **)&sv->oc_jobs, sv->oc_slots * sizeof(ClusterJob));
     for (int k = 0; k < sv->oc_slots && e == cudaSuccess; ++k) {
         cudaStream_t st = nullptr;
         cudaEvent_t ev = nullptr;
-        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (sv->split.ctx[1]) {
+            if (!sm_partition_add_stream(sv->split, 1, &st)) e = cudaErrorUnknown;
+        } else {
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        }
         if (e == cudaSuccess) sv->oc_stream.push_back(st);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) sv->oc_ev.push_back(ev);
@@ -953,6 +976,8 @@ extern "C" int asyrk_server_get_stats(asyrk_server *sv, asyrk_server_stats *st)
     st->max_slots = sv->max_slots;
     st->max_active = (int32_t)sv->max_active;
     st->max_active_shared = (int32_t)sv->max_active_shared;
+    st->step_sms = sv->split.sms[0];
+    st->onchip_sms = sv->split.sms[1];
     st->fatal = sv->fatal;
     return ASYRK_OK;
 }
@@ -976,8 +1001,9 @@ extern "C" void asyrk_server_destroy(asyrk_server *sv)
         sv->reqs.clear();
     }
     cudaStreamSynchronize(sv->s);
-    cudaStreamDestroy(sv->s);
+    if (sv->s != sv->split.stream[0]) cudaStreamDestroy(sv->s);
     for (cudaStream_t x : sv->oc_stream) cudaStreamDestroy(x);
+    sm_partition_destroy(&sv->split);
     for (cudaEvent_t x : sv->oc_ev) cudaEventDestroy(x);
     cudaFree(sv->oc_jobs);
     cudaFree(sv->d);
