@@ -223,3 +223,27 @@ def test_admission_caps_the_warp_demand_of_the_shared_step(pool):
                 assert stt["max_active_shared"] == 1
             else:
                 assert stt["max_active_shared"] >= 2
+
+
+@pytest.mark.parametrize("partition", [0, -1])
+def test_onchip_requests_and_the_shared_step_on_split_sms(pool, partition):
+    # by default the on-chip requests get 16 SMs of their own and the shared
+    # step the rest (green contexts); -1 keeps one pool; results are the same
+    # either way: every request within its tolerance
+    import torch
+    systems, probs = pool
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    with asyrk.Server(8 << 30, max_slots=8, partition=partition) as sv:
+        jobs = [(2, asyrk.MODE_ASYNC, 1e-6), (0, asyrk.MODE_REFINE, 1e-10), (4, asyrk.MODE_ASYNC, 1e-6),
+                (3, asyrk.MODE_ASYNC, 1e-6), (1, asyrk.MODE_REFINE, 1e-10)]
+        ts = [sv.submit(probs[i], x_true=systems[i].x_true, tol=tol, mode=mode)
+              for i, mode, tol in jobs]
+        for (i, _, tol), t in zip(jobs, ts):
+            st, x, _ = sv.wait(t, systems[i].n, timeout_us=60_000_000)
+            assert st == asyrk.OK and _err(x, systems[i]) <= tol * 1.0001
+        stt = sv.stats()
+        if partition == 0:
+            assert stt["onchip_sms"] >= 16 and stt["step_sms"] + stt["onchip_sms"] == sms
+            assert stt["onchip_completed"] >= 3
+        else:
+            assert stt["onchip_sms"] == 0 and stt["step_sms"] == 0
