@@ -204,7 +204,8 @@ typedef struct asyrk_problem_stats {
  *   b      : m doubles, finite.
  * Host arrays are read before the call returns; device arrays too.
  * Errors: EINVAL (m, n outside [1, 2^31-1], a malformed CSR, a zero row,
- * non-finite data, bad opts), ENOMEM, ECUDA.  On error *out is NULL. */
+ * non-finite data, ||A||_F^2 or ||b||^2 beyond the FP64 range, bad opts),
+ * ENOMEM, ECUDA.  On error *out is NULL. */
 int asyrk_create(asyrk_problem **out, int64_t m, int64_t n, const int64_t *row_ptr,
                  const int32_t *col_idx, const void *values, int vdtype, const double *b,
                  const asyrk_create_opts *opts);

@@ -380,6 +380,7 @@ int row_totals_and_alias(asyrk_problem *p, cudaStream_t s)
     ASYRK_CK(cudaStreamSynchronize(s));
     if (!(h_sums[0] > 0.0) || !isfinite(h_sums[0]))
         return set_error(ASYRK_EINVAL, "||A||_F^2 is not finite");
+    if (!isfinite(h_sums[1])) return set_error(ASYRK_EINVAL, "||b||^2 is not finite");
     p->frob2 = h_sums[0];
     p->bnorm = sqrt(h_sums[1]);
     p->uniform = h_diff ? 0 : 1;

@@ -63,6 +63,23 @@ def test_malformed_problem_is_rejected(defect):
         assert oracle.validate(4, 6, row_ptr, col, val, b) == oracle.EINVAL
 
 
+@pytest.mark.parametrize("which", ["frobenius", "b"])
+def test_totals_beyond_the_fp64_range_are_rejected(which):
+    # every value and every row weight is finite, but ||A||_F^2 (four rows of
+    # weight 1e308) or ||b||^2 (b_i = 1e200) is not: the exact sums carry into
+    # their top digits and round to infinity, and create refuses the problem
+    row_ptr = np.arange(5, dtype=np.int64)
+    col = np.arange(4, dtype=np.int32)
+    val = np.full(4, 1e154) if which == "frobenius" else np.ones(4)
+    b = np.ones(4) if which == "frobenius" else np.full(4, 1e200)
+    st, h = asyrk.asyrk_create(4, 4, row_ptr, col, val, asyrk.F64, b)
+    assert st == asyrk.EINVAL and not h.value
+    assert "not finite" in asyrk.asyrk_last_error()
+    if which == "frobenius":  # the oracle's F overflows the same way
+        assert oracle.validate(4, 4, row_ptr, col, val, b) == oracle.OK
+        assert oracle.row_weights(4, row_ptr, val)[1] == np.inf
+
+
 def test_well_formed_base_is_accepted():
     row_ptr, col, val, b = _base()
     with asyrk.Problem(4, 6, row_ptr, col, val, asyrk.F64, b) as p:
