@@ -325,11 +325,12 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
         D.n = (unsigned)p->n;
         D.dtype = p->dtype;
         D.uniform = p->uniform;
-        // the plan splits the warps in proportion to this: a sweep's time
-        // grows with the stored entries and, by a fixed latency per
-        // projection, with the rows (measured on the 256-system workload:
-        // 89-90 ms with the global engine alone against 92 ms for entries only)
-        D.work = (double)p->nnz + 16.0 * (double)p->m;
+        // the plan splits the warps in proportion to this.  A worker's
+        // projection takes about 3.6 us + 0.63 us per entry a lane handles
+        // (L/G of them; measured per slot on the 256-system workload), and a
+        // sweep lasts m / workers = m G / (32 warps) projections of it, so
+        // equal sweeps want warps in proportion to m (5.7 G + L)
+        D.work = (double)p->m * (6.0 * (double)G) + (double)p->nnz;
         D.key = make_uint2((unsigned)p->seed, (unsigned)(p->seed >> 32));
         D.rec = p->rec;
         D.col = p->col;

@@ -84,7 +84,14 @@ bool sm_partition_create(int dev, int first, SmPartition *out)
     p.ctx[0] = c0;
     ok = ok && create(&c1, d1, (CUdevice)dev, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS;
     p.ctx[1] = c1;
-    ok = ok && screate(&s0, c0, CU_STREAM_NON_BLOCKING, 0) == CUDA_SUCCESS;
+    // group 0's stream at the highest priority: where the groups share a
+    // hardware queue, its launches go first
+    int lo_prio = 0, hi_prio = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess) {
+        (void)cudaGetLastError();
+        hi_prio = 0;
+    }
+    ok = ok && screate(&s0, c0, CU_STREAM_NON_BLOCKING, hi_prio) == CUDA_SUCCESS;
     p.stream[0] = (cudaStream_t)s0;
     ok = ok && screate(&s1, c1, CU_STREAM_NON_BLOCKING, 0) == CUDA_SUCCESS;
     p.stream[1] = (cudaStream_t)s1;

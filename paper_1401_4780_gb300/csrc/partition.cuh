@@ -11,6 +11,7 @@ namespace asyrk {
 struct SmPartition {
     void *ctx[2] = {nullptr, nullptr};            // CUgreenCtx of each group
     cudaStream_t stream[2] = {nullptr, nullptr};  // a non-blocking stream in each group
+                                                  // (group 0's at the highest priority)
     int sms[2] = {0, 0};                          // SMs of each group
 };
 
