@@ -71,6 +71,7 @@ struct asyrk_batch {
     // both engines at once: the SMs split between them (stream 0 global, 1 on-chip)
     asyrk::SmPartition split;
     int resident_warps_glob = 0;         // the global engine's warps on its SMs
+    int *onchip_list = nullptr;          // device: on-chip members grouped per launch
     cudaEvent_t ev_on_join = nullptr;
 };
 
@@ -88,6 +89,7 @@ static void batch_free(asyrk_batch *b)
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->ev_on_join) cudaEventDestroy(b->ev_on_join);
     sm_partition_destroy(&b->split);
+    cudaFree(b->onchip_list);
     cudaFree(b->d);
     cudaFree(b->x);
     cudaFree(b->x64);
@@ -144,12 +146,56 @@ static int build_graph(asyrk_batch *b)
 
 // The on-chip engine's graph: one kernel node per on-chip member, no
 // dependencies, the longest estimated solves placed first.
-static int build_onchip_graph(asyrk_batch *b)
+static int build_onchip_graph(asyrk_batch *b, bool grouped)
 {
     ASYRK_CK(cudaGraphCreate(&b->g_on, 0));
-    for (int k : b->order) {
-        int st = cluster_add_node(b->g_on, b->probs[k]->dtype, b->shapes[k], b->jobs, k);
+    if (!grouped) {
+        for (int k : b->order) {
+            int st = cluster_add_node(b->g_on, b->probs[k]->dtype, b->shapes[k], b->jobs, k);
+            if (st != ASYRK_OK) return st;
+        }
+        ASYRK_CK(cudaGraphInstantiate(&b->exec_on, b->g_on, 0));
+        return ASYRK_OK;
+    }
+    // members with the same value type and sub-warp width, and threads and
+    // shared memory in the same bucket (threads to a multiple of 128, memory to
+    // a power of two from 8 KiB), share one launch whose CTA b solves the b-th
+    // longest of them: a few dozen launches instead of one per member, whose
+    // burst of pending launches at the start held up the other engine's graph
+    std::vector<std::vector<int>> groups;
+    std::vector<long long> keys;
+    for (int k : b->order) {  // longest estimated solve first
+        const ClusterShape &sh = b->shapes[k];
+        const long long thr = (sh.threads + 127) / 128;
+        long long mem = 8192;
+        while (mem < (long long)sh.smem) mem *= 2;
+        const long long key = (((long long)b->probs[k]->dtype * 64 + sh.G) * 16 + thr) * 64 +
+                              (long long)log2((double)mem);
+        const size_t q = (size_t)(std::find(keys.begin(), keys.end(), key) - keys.begin());
+        if (q == keys.size()) {
+            keys.push_back(key);
+            groups.emplace_back();
+        }
+        groups[q].push_back(k);
+    }
+    std::vector<int> flat;
+    for (auto &g : groups) flat.insert(flat.end(), g.begin(), g.end());
+    ASYRK_CK(cudaMalloc((void **)&b->onchip_list, flat.size() * sizeof(int)));
+    ASYRK_CK(cudaMemcpy(b->onchip_list, flat.data(), flat.size() * sizeof(int),
+                        cudaMemcpyHostToDevice));
+    size_t off = 0;
+    for (auto &g : groups) {  // in the order of their longest members
+        int threads = 0;
+        size_t smem = 0;
+        for (int k : g) {
+            threads = std::max(threads, b->shapes[k].threads);
+            smem = std::max(smem, b->shapes[k].smem);
+        }
+        const int k0 = g[0];
+        int st = cluster_add_list_node(b->g_on, b->probs[k0]->dtype, b->shapes[k0].G, threads, smem,
+                                       (int)g.size(), b->jobs, b->onchip_list + off);
         if (st != ASYRK_OK) return st;
+        off += g.size();
     }
     ASYRK_CK(cudaGraphInstantiate(&b->exec_on, b->g_on, 0));
     return ASYRK_OK;
@@ -410,7 +456,6 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
         if (e == cudaSuccess && b->n_glob > 0)
             e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
         if (e != cudaSuccess) return fail(cuda_fail(e, "on-chip batch set-up", __FILE__, __LINE__));
-        if (b->graph && (st = build_onchip_graph(b)) != ASYRK_OK) return fail(st);
     }
     if (b->n_glob > 0 && b->n_on > 0 && b->graph && o.partition >= 0) {
         // SMs for the on-chip engine: its members' thread-time per sweep within
@@ -434,6 +479,8 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
                 return fail(cuda_fail(cudaGetLastError(), "batch event", __FILE__, __LINE__));
         }
     }
+    if (b->n_on > 0 && b->graph && (st = build_onchip_graph(b, b->split.ctx[1] != nullptr)) != ASYRK_OK)
+        return fail(st);
     if (b->n_glob > 0 && b->graph && (st = build_graph(b)) != ASYRK_OK) return fail(st);
     *out = b;
     return ASYRK_OK;

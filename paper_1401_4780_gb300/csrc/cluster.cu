@@ -288,7 +288,7 @@ __device__ __forceinline__ void prefetch_draw(unsigned long long j, const Cluste
 }
 
 template <typename VT, int G, bool DS>
-__global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1) k_cluster_solve(ClusterJob *jobs, int k)
+__device__ __forceinline__ void cluster_solve(ClusterJob *jobs, int k)
 {
     extern __shared__ __align__(16) unsigned char cl_dyn[];
     __shared__ double wsum[2 * (CLUSTER_MAX_THREADS / 32)];
@@ -573,6 +573,21 @@ __global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1) k_cluster_solve(Cluste
     cl_sync<DS>();  // no CTA leaves while another may still read its shared memory
 }
 
+// one member's solve: jobs[k] (a cluster of C CTAs, or one CTA)
+template <typename VT, int G, bool DS>
+__global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1) k_cluster_solve(ClusterJob *jobs, int k)
+{
+    cluster_solve<VT, G, DS>(jobs, k);
+}
+
+// many one-CTA members in one launch: CTA b solves jobs[list[b]]
+template <typename VT, int G>
+__global__ void __launch_bounds__(CLUSTER_MAX_THREADS, 1)
+    k_cluster_solve_list(ClusterJob *jobs, const int *__restrict__ list)
+{
+    cluster_solve<VT, G, false>(jobs, list[blockIdx.x]);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -717,6 +732,44 @@ int cluster_add_node(cudaGraph_t g, int dtype, const ClusterShape &sh, ClusterJo
         v.clusterDim.z = 1;
         ASYRK_CK(cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeClusterDimension, &v));
     }
+    return ASYRK_OK;
+}
+
+using ClusterListKernel = void (*)(ClusterJob *, const int *);
+
+template <typename VT>
+static ClusterListKernel pick_list_g(int G)
+{
+    switch (G) {
+    case 1: return k_cluster_solve_list<VT, 1>;
+    case 2: return k_cluster_solve_list<VT, 2>;
+    case 4: return k_cluster_solve_list<VT, 4>;
+    case 8: return k_cluster_solve_list<VT, 8>;
+    case 16: return k_cluster_solve_list<VT, 16>;
+    case 32: return k_cluster_solve_list<VT, 32>;
+    default: return nullptr;
+    }
+}
+
+int cluster_add_list_node(cudaGraph_t g, int dtype, int G, int threads, size_t smem, int ctas,
+                          ClusterJob *jobs, const int *list)
+{
+    ClusterListKernel fn = dtype == ASYRK_BF16 ? pick_list_g<bf16_t>(G) : pick_list_g<float>(G);
+    if (!fn || ctas < 1) return set_error(ASYRK_EINVAL, "no on-chip kernel for subwarp %d", G);
+    if (smem > 48 * 1024) {
+        ASYRK_CK(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)CLUSTER_SMEM_BYTES));
+    }
+    void *args[2] = {&jobs, &list};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.func = (void *)fn;
+    kp.gridDim = dim3((unsigned)ctas);
+    kp.blockDim = dim3((unsigned)threads);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    cudaGraphNode_t node;
+    ASYRK_CK(cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp));
     return ASYRK_OK;
 }
 

@@ -95,6 +95,11 @@ int cluster_prepare(int dtype, int G, int C);
 int cluster_check_schedulable(int dtype, const ClusterShape &sh);
 // The solve of jobs[k] as a kernel node of g (no dependencies).
 int cluster_add_node(cudaGraph_t g, int dtype, const ClusterShape &sh, ClusterJob *jobs, int k);
+// One kernel node of g solving several one-CTA members: CTA b solves
+// jobs[list[b]] (list: `ctas` device ints), every CTA with `threads` threads and
+// `smem` bytes of dynamic shared memory (at least each member's own).
+int cluster_add_list_node(cudaGraph_t g, int dtype, int G, int threads, size_t smem, int ctas,
+                          ClusterJob *jobs, const int *list);
 // The solve of jobs[k] launched on s.
 int cluster_launch(int dtype, const ClusterShape &sh, ClusterJob *jobs, int k, cudaStream_t s);
 
