@@ -22,6 +22,10 @@ namespace asyrk {
 constexpr int BATCH_ERR_CHUNK = 16384;  // x entries per check block (x* measure)
 constexpr int BATCH_ROW_CHUNK = 2048;   // rows per check block (residual measure)
 constexpr int BATCH_MAX_SLOTS = 4096;   // slots the plan kernel can place
+// projections per worker a server step runs at least (a lone large request of
+// the served workload sweeps in ~50 per worker), capped per slot by the
+// sweeps its measured contraction says it still needs; only the server's steps
+constexpr double SERVER_STEP_CHAIN = 512.0;
 
 struct SysDesc {
     const RowRec *rec;

@@ -125,7 +125,12 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_batch_plan(SysDesc *d, int cou
 #pragma unroll
     for (int q = 0; q < PLAN_PER_THREAD; ++q)
         if (on[q] && w[q] > 0 && chain[q] / w[q] > tl) tl = chain[q] / w[q];
-    const double tmax = block_all(tl, max_d, shd);
+    double tmax = block_all(tl, max_d, shd);
+    // the server's step runs at least SERVER_STEP_CHAIN projections per worker,
+    // so that a lone request whose sweep is short does several sweeps per step
+    // and pays the step's fixed cost (plan, check, the host's round trip) less
+    // often; it checks its tolerance once per step
+    if (even_share && tmax < SERVER_STEP_CHAIN) tmax = SERVER_STEP_CHAIN;
     // warp ranges: exclusive prefix of the warps in slot order, one stride row
     // (slots q*PLAN_THREADS .. q*PLAN_THREADS + PLAN_THREADS - 1) at a time
     long long base = 0;
@@ -149,6 +154,22 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_batch_plan(SysDesc *d, int cou
                 const long long left_sw = d[s].max_sweeps - d[s].sweeps;
                 if (kmax > left_sw) kmax = left_sw > 1 ? left_sw : 1;
                 kk = kf >= (double)kmax ? (int)kmax : (kf < 1.0 ? 1 : (int)kf);
+            }
+            if (even_share && on[q] && kk > 1) {
+                // server steps: no more sweeps than the slot still needs at the
+                // contraction per sweep it has shown (its measure over its first,
+                // or for an inner solve of refinement, over 1 at d = 0)
+                const SysDesc &D = d[s];
+                const bool inner = D.mode == SLOT_REFINE;
+                const long long done = inner ? D.inner_sweeps : D.sweeps;
+                const double m0 = inner ? 1.0 : D.meas0;
+                const double target = inner ? D.inner_tol : D.tol;
+                if (done > 0 && D.meas > 0.0 && m0 > 0.0 && D.meas < m0 && target > 0.0 &&
+                    target < D.meas) {
+                    const double rho = pow(D.meas / m0, 1.0 / (double)done);
+                    const double rem = log(target / D.meas) / log(rho);
+                    if (rem < (double)kk) kk = rem < 1.0 ? 1 : (int)ceil(rem);
+                }
             }
             d[s].warp0 = (int)w0;
             d[s].nwarps = (int)nw;
