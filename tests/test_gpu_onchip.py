@@ -226,3 +226,31 @@ def test_hybrid_batch_reaches_tolerance(graph, partition):
             assert p.position == info.sweeps * s.m
     finally:
         _close(probs)
+
+
+def test_grouped_onchip_launches_match_the_sequential_oracle_iterate():
+    # in a hybrid batch on split SMs the on-chip members run grouped, several
+    # per launch (one CTA each); with one worker each, every on-chip member's
+    # iterate after two sweeps is the oracle's sequential RK iterate to FP32
+    # accuracy, as it is with one launch per member
+    # (the global member, 2^21 x 4096, does not fit a CTA and its Corollary 2
+    # cap keeps its sweep long, so the one-worker on-chip members stay on-chip)
+    small = [synth.make_system(512 + 256 * k, 128 + 64 * k, 8 + 4 * k, 60 + k,
+                               row_norms="lognormal", value_dtype="f32") for k in range(6)]
+    big = synth.make_system(1 << 21, 4096, 8, 66, row_norms="unit", value_dtype="f32")
+    systems = small + [big]
+    probs = [asyrk.Problem.from_system(s) for s in systems]
+    try:
+        with asyrk.Batch(probs, workers=1) as b:
+            xs = [np.zeros(s.n) for s in systems]
+            _, infos, bi = b.solve(xs, tols=[0.0] * len(systems), max_sweeps=2)
+            assert bi.engine == asyrk.ENGINE_ONCHIP | asyrk.ENGINE_GLOBAL
+            assert bi.onchip_members == len(small) and bi.global_sms > 0
+        for s, x, info in zip(small, xs, infos):
+            assert info.workers == 1 and info.sweeps == 2
+            xo = np.zeros(s.n)
+            oracle.rk_steps(s.m, s.n, s.row_ptr, s.col, s.val64, s.b, xo, 1.0,
+                            synth.solver_seed(s.seed), 0, 0, 2 * s.m)
+            assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 2e-5, s.m
+    finally:
+        _close(probs)
