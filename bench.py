@@ -980,6 +980,16 @@ def run_asyrk(args, dist):
                                 "sweeps": info.sweeps, "rel_err": info.rel_err,
                                 "applied_projections_per_s":
                                     (info.projections - info.skipped) / info.seconds})
+        # time to 1e-8 on the same system: FP32 values and FP32 inner solves
+        # with FP64 refinement (the plain FP32 kernel stalls near 1e-7)
+        x.zero_()
+        torch.cuda.synchronize()
+        st, info = p.solve(x, gamma=1.0, tol=1e-8, max_sweeps=max_sweeps, x_true=xt,
+                           device_ptrs=True, stream=stream, mode=asyrk.MODE_REFINE)
+        gamma_sweep.append({"mode": "refine", "tol": 1e-8, "status": st,
+                            "ms": 1e3 * info.seconds, "sweeps": info.sweeps,
+                            "refine_steps": info.refine_steps, "rel_err": info.rel_err,
+                            "rel_res": info.rel_res})
     p.close()
 
     # ---------------- end to end from host buffers ----------------
