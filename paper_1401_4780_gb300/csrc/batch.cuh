@@ -68,6 +68,8 @@ struct SysDesc {
     int phase;            // 0: projections; 1: outer step pending
     float *r32;
     double inner_tol;     // inner solve: ||r - A d|| / ||r|| target
+    double inner_goal;    // this outer step's inner target: inner_tol, or the
+                          // reduction the tolerance still needs when closer
     long long inner_sweeps, max_inner;
     int outer_steps;
     unsigned out_count;   // last-block counter of the outer step
@@ -79,6 +81,18 @@ struct SysDesc {
     int shuf_h;           // half width of the shuffle's Feistel domain
     int pad2;
 };
+// The inner target of an outer refinement step: inner_tol, or, when the outer
+// measure `meas` is within a factor 1/inner_tol of the tolerance, half the
+// reduction it still needs (at most 1/2), so the last inner solve stops near
+// the tolerance instead of far below it.
+__host__ __device__ __forceinline__ double refine_inner_goal(double inner_tol, double tol,
+                                                             double meas)
+{
+    if (!(tol > 0.0) || !(meas > 0.0)) return inner_tol;
+    const double need = 0.5 * tol / meas;
+    return need > inner_tol ? (need < 0.5 ? need : 0.5) : inner_tol;
+}
+
 
 constexpr int SLOT_PLAIN = 0;
 constexpr int SLOT_REFINE = 1;

@@ -262,6 +262,7 @@ struct SolveState {
     double meas, meas0;  // last and first measure
     double ref_in;       // refinement: ||r|| of the current inner solve
     double res2;         // refinement: ||b - A x64||^2 of the last outer step
+    double inner_goal;   // refinement: this outer step's inner target
     long long sweeps, inner_sweeps;
     int status, outer_steps;
     int done, outer_next;
@@ -332,6 +333,7 @@ __device__ __forceinline__ void cluster_solve(ClusterJob *jobs, int k)
         ss.meas = ss.meas0 = -1.0;
         ss.ref_in = 1.0;
         ss.res2 = 0.0;
+        ss.inner_goal = J.inner_tol;
         ss.status = ASYRK_NOT_CONVERGED;
         ss.outer_steps = 0;
         ss.inner_sweeps = 0;
@@ -392,6 +394,7 @@ __device__ __forceinline__ void cluster_solve(ClusterJob *jobs, int k)
                 ss.outer_next = 0;
                 ss.ref_in = rnorm;
                 ss.inner_sweeps = 0;
+                ss.inner_goal = refine_inner_goal(J.inner_tol, J.tol, meas);
             }
             cl_sync<DS>();  // r32 complete before the inner solve reads it; decisions visible
             continue;
@@ -529,7 +532,7 @@ __device__ __forceinline__ void cluster_solve(ClusterJob *jobs, int k)
                 if (!isfinite(mi)) {
                     ss.status = ASYRK_DIVERGED;
                     ss.done = 1;
-                } else if (mi <= J.inner_tol || ss.inner_sweeps >= J.max_inner ||
+                } else if (mi <= ss.inner_goal || ss.inner_sweeps >= J.max_inner ||
                            ss.sweeps >= J.max_sweeps) {
                     ss.outer_next = 1;
                 }

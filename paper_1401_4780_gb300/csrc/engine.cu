@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_batch_plan(SysDesc *d, int cou
                 const bool inner = D.mode == SLOT_REFINE;
                 const long long done = inner ? D.inner_sweeps : D.sweeps;
                 const double m0 = inner ? 1.0 : D.meas0;
-                const double target = inner ? D.inner_tol : D.tol;
+                const double target = inner ? D.inner_goal : D.tol;
                 if (done > 0 && D.meas > 0.0 && m0 > 0.0 && D.meas < m0 && target > 0.0 &&
                     target < D.meas) {
                     const double rho = pow(D.meas / m0, 1.0 / (double)done);
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256) k_batch_check(SysDesc *d, int count, doub
         if (!isfinite(meas)) {
             D.active = 0;
             D.status = ASYRK_DIVERGED;
-        } else if (meas <= D.inner_tol || D.inner_sweeps >= D.max_inner ||
+        } else if (meas <= D.inner_goal || D.inner_sweeps >= D.max_inner ||
                    D.sweeps >= D.max_sweeps) {
             D.phase = 1;
         }
@@ -525,6 +525,7 @@ __global__ void __launch_bounds__(256) k_batch_outer_residual(SysDesc *d, int co
         D.phase = 0;  // next inner solve of A d = r
         D.ref = rnorm;
         D.inner_sweeps = 0;
+        D.inner_goal = refine_inner_goal(D.inner_tol, D.tol, meas);
     }
 }
 

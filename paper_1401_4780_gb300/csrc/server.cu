@@ -321,6 +321,7 @@ static bool admit_locked(asyrk_server *sv, Request *r, int k)
     D.ref = has_xt ? (xtn > 0.0 ? xtn : 1.0) : bn;
     D.outer_ref = D.ref;
     D.inner_tol = sv->inner_tol;
+    D.inner_goal = sv->inner_tol;
     D.max_inner = sv->max_inner;
     D.max_k = 32;  // short sweeps run several per engine step
     D.sampling = ASYRK_SAMPLE_WEIGHTED;

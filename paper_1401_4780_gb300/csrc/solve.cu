@@ -419,11 +419,19 @@ static int solve_refine(SolveCtx &c, double gamma, double tol, int64_t max_sweep
         if (diverged(meas, meas0)) { status = ASYRK_DIVERGED; break; }
         if (tol > 0.0 && meas <= tol) { status = ASYRK_OK; break; }
         if (sweeps >= max_sweeps) break;
+        // this step's inner target: inner_tol, or, when the tolerance is
+        // closer than that, just the reduction it still needs (with a margin
+        // of 2), so the last inner solve does not overshoot the tolerance
+        double step_tol = inner_tol;
+        if (tol > 0.0 && (c.kind == MEAS_ERR || c.kind == MEAS_RES) && meas > 0.0) {
+            const double need = 0.5 * tol / meas;
+            if (need > step_tol) step_tol = need < 0.5 ? need : 0.5;
+        }
         if (o.inner_sweeps <= 0 && rprev > 0.0 && rnorm > 0.0) {
             // adapt the inner sweep count to the contraction the last step achieved
             const double rho = rnorm / rprev;
             if (rho > 0.0 && rho < 1.0) {
-                double want = (double)inner * log(inner_tol) / log(rho);
+                double want = (double)inner * log(step_tol) / log(rho);
                 if (want < 2.0) want = 2.0;
                 if (want > 4.0 * inner) want = 4.0 * inner;
                 inner = (int64_t)ceil(want);
