@@ -325,6 +325,7 @@ def workload_config(s, args):
                         if args.scale == 0 else "reduced large async system (testing)",
             "m": s.m, "n": s.n, "nnz_per_row": 32, "nnz": s.nnz, "gamma": args.gamma,
             "tol": args.tol, "x0": "zeros", "step": "one solve to tol from x0",
+            "check_interval": "adaptive (check_every=0)",
             "l2_flush": "none: 1.07 GB column/value stream > 129 MB L2 per sweep",
             "parallelism": "replicas (one independent system per GPU)"}
 
@@ -865,8 +866,11 @@ def run_asyrk(args, dist):
 
     def step():
         x.zero_()
+        # check_every = 0: the solve's adaptive check interval (next check after
+        # half the sweeps the measured contraction still needs); it stops at
+        # most 10 % past the sweep that meets the tolerance
         st, info = p.solve(x, gamma=args.gamma, tol=args.tol, max_sweeps=max_sweeps, x_true=xt,
-                           device_ptrs=True, stream=stream, profile=True)
+                           device_ptrs=True, stream=stream, profile=True, check_every=0)
         if st != asyrk.OK:
             raise RuntimeError("solve status %d: %s" % (st, asyrk.asyrk_last_error()))
         return info
@@ -901,7 +905,14 @@ def run_asyrk(args, dist):
     per_launch_proj = proj / proj_launches
     achieved = BYTES_PER_PROJECTION * per_launch_proj / per_launch_s / 1e9
     peak, peak_kind = read_peaks()
+    # the committed ncu summary holds DRAM bytes for a launch of one sweep
+    # (4,194,304 drawn projections); a launch here may run several sweeps (the
+    # adaptive check interval), so the bytes are scaled by the drawn
+    # projections per launch (the stream is read once per projection)
     traffic = recorded_traffic()
+    if traffic is not None:
+        drawn_per_launch = (proj + skipped) / proj_launches
+        traffic = traffic * drawn_per_launch / float(1 << 22) if args.scale == 0 else None
     sweeps = [i.sweeps for i in infos]
     # L2 denominators measured now on this GPU: random red.add.f32 and gathers
     # on an array the size of x (the kernel does 32 of each per projection)
@@ -975,7 +986,7 @@ def run_asyrk(args, dist):
             x.zero_()
             torch.cuda.synchronize()
             st, info = p.solve(x, gamma=g, tol=args.tol, max_sweeps=max_sweeps, x_true=xt,
-                               device_ptrs=True, stream=stream, profile=True)
+                               device_ptrs=True, stream=stream, profile=True, check_every=0)
             gamma_sweep.append({"gamma": g, "status": st, "ms": 1e3 * info.seconds,
                                 "sweeps": info.sweeps, "rel_err": info.rel_err,
                                 "applied_projections_per_s":
@@ -1024,7 +1035,7 @@ def run_asyrk(args, dist):
             t1 = time.perf_counter()
             h_x.zero_()
             st, info = q.solve(h_x, gamma=args.gamma, tol=args.tol, max_sweeps=max_sweeps,
-                               x_true=h_xt)
+                               x_true=h_xt, check_every=0)
             t2 = time.perf_counter()
         dt = time.perf_counter() - t0
         if k > 0:
