@@ -1053,8 +1053,9 @@ def run_asyrk(args, dist):
     e2e_proj = dist.reduce(e2e_proj, "sum")
     # what crosses the host link per step: asyrk_create copies the CSR arrays and
     # b (the row records and the alias table are built on the GPU); the solve
-    # copies x0 and x* in and x out, and reads one 8-byte measure per check (a
-    # check after every sweep, plus the initial one) and a few status words
+    # copies x0 and x* in and x out, and reads one 8-byte measure per check (at
+    # most one per sweep with the adaptive interval, plus the initial one: counted
+    # as one per sweep) and a few status words
     h2d = (s.row_ptr.nbytes + s.col.nbytes + s.val_store.nbytes + s.b.nbytes
            + 2 * 8 * s.n)
     checks = e2e_sweeps / max(1, args.e2e_steps) + 1
@@ -1065,10 +1066,9 @@ def run_asyrk(args, dist):
            "ms_per_step_split": {k: 1e3 * v / max(1, args.e2e_steps) for k, v in split.items()},
            "create_ms_each_step": create_ms,
            "host_affinity": affinity, "h2d_probe_gbs": h2d_gbs,
-           "note": "create copies 1.1 GB over the host link (~210 GB/s: ~5.5 ms of its ~9 ms); "
-                   "the link is shared with the other GPUs' jobs on the same host, and runs saw "
-                   "periodic stretches at a fraction of that rate that slow some creates to "
-                   "20-200 ms"}
+           "note": "create copies 1.1 GB over the host link (~210 GB/s: ~5.2 ms of its ~7.4 ms); "
+                   "on some boxes the link stalls for 10-60 ms about every 0.5 s whatever the "
+                   "process runs, which slows the creates that meet a stall to 16-240 ms"}
 
     cpu = None
     cpu_mt = None

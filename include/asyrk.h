@@ -213,6 +213,14 @@ int asyrk_create(asyrk_problem **out, int64_t m, int64_t n, const int64_t *row_p
 /* Release the handle and its device memory (NULL is ignored). */
 void asyrk_destroy(asyrk_problem *p);
 
+/* Problems' device memory (arrays, set-up temporaries, solve workspace) comes
+ * from one stream-ordered memory pool per device.  Memory that asyrk_destroy
+ * frees stays in the pool, up to 1/8 of the device's memory and at most 16 GiB,
+ * for the next asyrk_create on that device.  This call waits for the current
+ * device and returns all the pool's unused memory to the driver.
+ * Returns ASYRK_OK or ECUDA. */
+int asyrk_trim_memory(void);
+
 /* Run the method from x (in: x0, out: the final iterate; n doubles, host or
  * device per opts->device_ptrs) with step-length factor gamma in (0, 2)
  * (sequential RK contracts only there: the derivation before Eq. (3) gives a

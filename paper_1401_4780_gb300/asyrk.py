@@ -87,7 +87,7 @@ EXPORTS = ["asyrk_create", "asyrk_destroy", "asyrk_solve", "asyrk_residual", "as
            "asyrk_batch_destroy", "asyrk_server_create", "asyrk_server_submit",
            "asyrk_server_wait", "asyrk_server_cancel", "asyrk_server_get_stats",
            "asyrk_server_destroy", "asyrk_lsq_create", "asyrk_lsq_solution",
-           "asyrk_lsq_params", "asyrk_spectrum_estimate"]
+           "asyrk_lsq_params", "asyrk_spectrum_estimate", "asyrk_trim_memory"]
 NOALLOC_MAX_ROWS = 16777216
 PROBE_RED_F32, PROBE_GATHER_F32, PROBE_GATHER_RED, PROBE_STREAM = 0, 1, 2, 3
 
@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH):
     lib.asyrk_spectrum_estimate.restype = ctypes.c_int
     lib.asyrk_destroy.argtypes = [P]
     lib.asyrk_destroy.restype = None
+    lib.asyrk_trim_memory.argtypes = []
+    lib.asyrk_trim_memory.restype = ctypes.c_int
     lib.asyrk_solve.argtypes = [P, P, f64, f64, i64, ctypes.POINTER(SolveOpts),
                                 ctypes.POINTER(SolveInfo)]
     lib.asyrk_solve.restype = ctypes.c_int
@@ -305,6 +307,11 @@ def asyrk_spectrum_estimate(m, n, row_ptr, col_idx, values, vdtype, steps=0, see
 
 def asyrk_destroy(h):
     load().asyrk_destroy(h)
+
+
+def asyrk_trim_memory() -> int:
+    """Return the unused memory of the current device's problem memory pool to the driver."""
+    return load().asyrk_trim_memory()
 
 
 def asyrk_solve(h, x, gamma, tol, max_sweeps, opts: SolveOpts = None):

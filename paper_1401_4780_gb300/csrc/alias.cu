@@ -24,6 +24,7 @@
 // heavy when the current one falls below one bucket, so both forms give the
 // same thresholds and aliases.
 #include "alias.cuh"
+#include "devmem.cuh"
 #include "scan.cuh"
 
 namespace asyrk {
@@ -326,26 +327,24 @@ __global__ void k_alias_heavies(int64_t L, int64_t H, const long long *__restric
     rec[h].alias = (unsigned)idx[L + t + 1];
 }
 
+// temporaries from the problems' pool, ordered on the set-up stream and
+// handed back on it when the set-up ends
 struct Tmp {
+    cudaStream_t s;
     void *ptrs[16] = {};
     int n = 0;
+    explicit Tmp(cudaStream_t stream) : s(stream) {}
     template <typename T>
     int alloc(T **p, size_t count)
     {
-        *p = nullptr;
-        cudaError_t e = cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            *p = nullptr;
-            return set_error(e == cudaErrorMemoryAllocation ? ASYRK_ENOMEM : ASYRK_ECUDA,
-                             "cudaMalloc of %zu bytes failed", count * sizeof(T));
-        }
+        const int st = devmem_alloc_n(p, count, s);
+        if (st != ASYRK_OK) return st;
         ptrs[n++] = (void *)*p;
         return ASYRK_OK;
     }
     ~Tmp()
     {
-        for (int k = 0; k < n; ++k) cudaFree(ptrs[k]);
+        for (int k = 0; k < n; ++k) devmem_free(ptrs[k], s);
     }
 };
 
@@ -354,7 +353,7 @@ struct Tmp {
 int row_totals_and_alias(asyrk_problem *p, cudaStream_t s)
 {
     const int64_t m = p->m;
-    Tmp t;
+    Tmp t(s);
     double *sums;  // sums: F, ||b||^2
     unsigned *differs;
     unsigned long long *acc;    // sum of masses, max mass, first row of max mass

@@ -7,6 +7,7 @@
 // The residual kernel also serves the refinement loop: r = b - A x64 in FP64,
 // optionally stored (rounded to FP32) as the right-hand side of the inner solve.
 #include "common.cuh"
+#include "devmem.cuh"
 
 namespace asyrk {
 
@@ -280,7 +281,8 @@ static void normal_vt(asyrk_problem *p, const void *x, bool x_f64, unsigned g, c
 int launch_normal_residual(asyrk_problem *p, const void *x, bool x_f64, int slot, cudaStream_t s)
 {
     if (!p->g64) {
-        ASYRK_CK(cudaMalloc((void **)&p->g64, p->n * sizeof(double)));
+        const int st = devmem_alloc_n(&p->g64, (size_t)p->n, s);  // ordered on s, used on s
+        if (st != ASYRK_OK) return st;
         p->dev_bytes += p->n * (int64_t)sizeof(double);
     }
     ASYRK_CK(cudaMemsetAsync(p->g64, 0, p->n * sizeof(double), s));

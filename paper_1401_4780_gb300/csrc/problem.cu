@@ -22,6 +22,7 @@
 
 #include "alias.cuh"
 #include "common.cuh"
+#include "devmem.cuh"
 #include "scan.cuh"
 
 namespace asyrk {
@@ -46,17 +47,11 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line)
 }
 
 template <typename T>
-static int dev_alloc(asyrk_problem *p, T **ptr, size_t count)
+static int dev_alloc(asyrk_problem *p, T **ptr, size_t count, cudaStream_t s)
 {
-    *ptr = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
-    if (e != cudaSuccess) {
-        *ptr = nullptr;
-        (void)cudaGetLastError();
-        return set_error(ASYRK_ENOMEM, "cudaMalloc of %zu bytes failed: %s",
-                         count * sizeof(T), cudaGetErrorString(e));
-    }
+    const int st = devmem_alloc_n(ptr, count, s);
+    if (st != ASYRK_OK) return st;
     p->dev_bytes += (int64_t)(count * sizeof(T));
     return ASYRK_OK;
 }
@@ -164,22 +159,23 @@ int ensure_workspace(asyrk_problem *p)
     if (p->ev[1]) return ASYRK_OK;
     int st;
     const size_t words = (size_t)((p->m + 31) / 32);
-    if (!p->xw && (st = dev_alloc(p, (double **)&p->xw, (size_t)p->n)) != ASYRK_OK) return st;
-    if (!p->x64 && (st = dev_alloc(p, &p->x64, (size_t)p->n)) != ASYRK_OK) return st;
-    if (!p->xt64 && (st = dev_alloc(p, &p->xt64, (size_t)p->n)) != ASYRK_OK) return st;
+    if (!p->xw && (st = dev_alloc(p, (double **)&p->xw, (size_t)p->n, nullptr)) != ASYRK_OK) return st;
+    if (!p->x64 && (st = dev_alloc(p, &p->x64, (size_t)p->n, nullptr)) != ASYRK_OK) return st;
+    if (!p->xt64 && (st = dev_alloc(p, &p->xt64, (size_t)p->n, nullptr)) != ASYRK_OK) return st;
     if (!p->red_part &&
-        (st = dev_alloc(p, &p->red_part, (size_t)ASYRK_MAX_RED_BLOCKS * 4)) != ASYRK_OK)
+        (st = dev_alloc(p, &p->red_part, (size_t)ASYRK_MAX_RED_BLOCKS * 4, nullptr)) != ASYRK_OK)
         return st;
     if (!p->red_count) {
-        if ((st = dev_alloc(p, &p->red_count, 1)) != ASYRK_OK) return st;
+        if ((st = dev_alloc(p, &p->red_count, 1, nullptr)) != ASYRK_OK) return st;
         ASYRK_CK(cudaMemset(p->red_count, 0, sizeof(unsigned)));
     }
-    if (!p->red_out && (st = dev_alloc(p, &p->red_out, 8)) != ASYRK_OK) return st;
+    if (!p->red_out && (st = dev_alloc(p, &p->red_out, 8, nullptr)) != ASYRK_OK) return st;
     if (!p->busy) {
-        if ((st = dev_alloc(p, &p->busy, words)) != ASYRK_OK) return st;
+        if ((st = dev_alloc(p, &p->busy, words, nullptr)) != ASYRK_OK) return st;
         ASYRK_CK(cudaMemset(p->busy, 0, words * sizeof(unsigned)));
     }
-    if (!p->skipped && (st = dev_alloc(p, &p->skipped, 1)) != ASYRK_OK) return st;
+    if (!p->skipped && (st = dev_alloc(p, &p->skipped, 1, nullptr)) != ASYRK_OK) return st;
+    ASYRK_CK(cudaStreamSynchronize(nullptr));  // the allocations, ordered on that stream
     if (!p->h_out) ASYRK_CK(cudaMallocHost((void **)&p->h_out, 8 * sizeof(double)));
     if (!p->ev[0]) ASYRK_CK(cudaEventCreate(&p->ev[0]));
     if (!p->ev[1]) ASYRK_CK(cudaEventCreate(&p->ev[1]));
@@ -192,25 +188,16 @@ static void free_problem(asyrk_problem *p)
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
-    cudaFree(p->rec);
-    cudaFree(p->col);
-    cudaFree(p->val);
-    cudaFree(p->b64);
-    cudaFree(p->w64);
-    cudaFree(p->xw);
-    cudaFree(p->x64);
-    cudaFree(p->xt64);
-    cudaFree(p->g64);
-    cudaFree(p->red_part);
-    cudaFree(p->red_count);
-    cudaFree(p->red_out);
-    cudaFree(p->rows_buf);
-    cudaFree(p->busy);
-    cudaFree(p->skipped);
+    // no work that uses the handle's memory may still run (cudaFree used to
+    // wait for the device the same way); the memory goes back to the pool
+    cudaDeviceSynchronize();
+    void *mem[] = {p->rec, p->col, p->val, p->b64, p->w64, p->xw, p->x64, p->xt64, p->g64,
+                   p->red_part, p->red_count, p->red_out, p->rows_buf, p->busy, p->skipped,
+                   p->loop_state};
+    for (void *q : mem) devmem_free(q, nullptr);
     if (p->h_out) cudaFreeHost(p->h_out);
     if (p->ev[0]) cudaEventDestroy(p->ev[0]);
     if (p->ev[1]) cudaEventDestroy(p->ev[1]);
-    cudaFree(p->loop_state);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
@@ -277,11 +264,18 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
     unsigned *err_d = nullptr;
     bool own_src = false;
     auto cleanup = [&]() {
-        if (!on_dev) { cudaFree(rp_d); cudaFree(b_d); }
-        if (own_src) { cudaFree(col_src); cudaFree(val_src); }
-        cudaFree(ps_d); cudaFree(plen_d); cudaFree(scan_tmp); cudaFree(info_d); cudaFree(err_d);
+        // back to the pool in the order of the stream that used them
+        if (!on_dev) { devmem_free(rp_d, s); devmem_free(b_d, s); }
+        if (own_src) { devmem_free(col_src, s); devmem_free(val_src, s); }
+        devmem_free(ps_d, s); devmem_free(plen_d, s); devmem_free(scan_tmp, s);
+        devmem_free(info_d, s); devmem_free(err_d, s);
     };
     auto fail = [&](int code) { cleanup(); return code; };
+#define ASYRK_ALLOC(ptr, bytes)                                                            \
+    do {                                                                                   \
+        const int st__ = devmem_alloc((void **)&(ptr), (bytes), s);                        \
+        if (st__ != ASYRK_OK) return fail(st__);                                           \
+    } while (0)
 #define ASYRK_CKC(call)                                                                    \
     do {                                                                                   \
         cudaError_t e__ = (call);                                                          \
@@ -292,13 +286,13 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
     if (on_dev) {
         rp_d = const_cast<int64_t *>(row_ptr);
     } else {
-        ASYRK_CKC(cudaMalloc((void **)&rp_d, (m + 1) * sizeof(int64_t)));
+        ASYRK_ALLOC(rp_d, (m + 1) * sizeof(int64_t));
         ASYRK_CKC(cudaMemcpyAsync(rp_d, row_ptr, (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     }
-    ASYRK_CKC(cudaMalloc((void **)&plen_d, m * sizeof(int64_t)));
-    ASYRK_CKC(cudaMalloc((void **)&ps_d, (m + 1) * sizeof(int64_t)));
-    ASYRK_CKC(cudaMalloc((void **)&scan_tmp, scan_tmp_count(m) * sizeof(int64_t)));
-    ASYRK_CKC(cudaMalloc((void **)&info_d, 3 * sizeof(unsigned long long)));
+    ASYRK_ALLOC(plen_d, m * sizeof(int64_t));
+    ASYRK_ALLOC(ps_d, (m + 1) * sizeof(int64_t));
+    ASYRK_ALLOC(scan_tmp, scan_tmp_count(m) * sizeof(int64_t));
+    ASYRK_ALLOC(info_d, 3 * sizeof(unsigned long long));
     ASYRK_CKC(cudaMemsetAsync(info_d, 0, 2 * sizeof(unsigned long long), s));
     ASYRK_CKC(cudaMemsetAsync(info_d + 2, 0xff, sizeof(unsigned long long), s));
     k_rowptr_pass<<<(unsigned)((m + RP_THREADS - 1) / RP_THREADS), RP_THREADS, 0, s>>>(m, n, rp_d, plen_d, info_d);
@@ -323,12 +317,12 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
 
     // 2. device arrays
     const size_t es = value_size(p->dtype);
-    if ((st = dev_alloc(p, &p->rec, (size_t)m)) != ASYRK_OK) return fail(st);
-    if ((st = dev_alloc(p, &p->col, (size_t)p->nnz_pad)) != ASYRK_OK) return fail(st);
-    if ((st = dev_alloc(p, (char **)&p->val, (size_t)p->nnz_pad * es)) != ASYRK_OK) return fail(st);
-    if ((st = dev_alloc(p, &p->b64, (size_t)m)) != ASYRK_OK) return fail(st);
-    if ((st = dev_alloc(p, &p->w64, (size_t)m)) != ASYRK_OK) return fail(st);
-    ASYRK_CKC(cudaMalloc((void **)&err_d, sizeof(unsigned)));
+    if ((st = dev_alloc(p, &p->rec, (size_t)m, s)) != ASYRK_OK) return fail(st);
+    if ((st = dev_alloc(p, &p->col, (size_t)p->nnz_pad, s)) != ASYRK_OK) return fail(st);
+    if ((st = dev_alloc(p, (char **)&p->val, (size_t)p->nnz_pad * es, s)) != ASYRK_OK) return fail(st);
+    if ((st = dev_alloc(p, &p->b64, (size_t)m, s)) != ASYRK_OK) return fail(st);
+    if ((st = dev_alloc(p, &p->w64, (size_t)m, s)) != ASYRK_OK) return fail(st);
+    ASYRK_ALLOC(err_d, sizeof(unsigned));
     ASYRK_CKC(cudaMemsetAsync(err_d, 0, sizeof(unsigned), s));
 
     // 3. the caller's entries: straight into place when rows are already
@@ -342,15 +336,15 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
         val_src = const_cast<void *>(values);
     } else {
         own_src = true;
-        ASYRK_CKC(cudaMalloc((void **)&col_src, p->nnz * 4));
-        ASYRK_CKC(cudaMalloc(&val_src, p->nnz * es));
+        ASYRK_ALLOC(col_src, p->nnz * 4);
+        ASYRK_ALLOC(val_src, p->nnz * es);
         ASYRK_CKC(cudaMemcpyAsync(col_src, col_idx, p->nnz * 4, cudaMemcpyHostToDevice, s));
         ASYRK_CKC(cudaMemcpyAsync(val_src, values, p->nnz * es, cudaMemcpyHostToDevice, s));
     }
     if (on_dev) {
         b_d = const_cast<double *>(b);
     } else {
-        ASYRK_CKC(cudaMalloc((void **)&b_d, m * sizeof(double)));
+        ASYRK_ALLOC(b_d, m * sizeof(double));
         ASYRK_CKC(cudaMemcpyAsync(b_d, b, m * sizeof(double), cudaMemcpyHostToDevice, s));
     }
     const int32_t *rs_col = aligned ? p->col : col_src;
@@ -378,6 +372,7 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
     if ((st = row_totals_and_alias(p, s)) != ASYRK_OK) return fail(st);
     cleanup();
 #undef ASYRK_CKC
+#undef ASYRK_ALLOC
     return ASYRK_OK;
 }
 
@@ -456,10 +451,12 @@ extern "C" int asyrk_draw_rows(asyrk_problem *p, uint64_t j0, int64_t count, uin
         return set_error(ASYRK_EINVAL, "bad argument");
     if (count == 0) return ASYRK_OK;
     if (count > p->rows_cap) {
-        cudaFree(p->rows_buf);
+        // the legacy default stream orders these with the launch and copy below
+        devmem_free(p->rows_buf, nullptr);
         p->rows_buf = nullptr;
         p->rows_cap = 0;
-        ASYRK_CK(cudaMalloc((void **)&p->rows_buf, count * sizeof(int32_t)));
+        const int st = devmem_alloc_n(&p->rows_buf, (size_t)count, nullptr);
+        if (st != ASYRK_OK) return st;
         p->rows_cap = count;
     }
     int st = launch_draw_rows(p, j0, count, stream_id, sampling, p->rows_buf, 0);

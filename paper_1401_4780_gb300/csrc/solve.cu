@@ -16,6 +16,7 @@
 #include <chrono>
 
 #include "batch.cuh"
+#include "devmem.cuh"
 
 namespace asyrk {
 
@@ -178,7 +179,9 @@ __global__ void k_loop_decide(LoopState *st, const double *red_out, int kind, do
 static int loop_resources(asyrk_problem *p)
 {
     if (!p->loop_state) {
-        ASYRK_CK(cudaMalloc(&p->loop_state, sizeof(LoopState)));
+        const int st = devmem_alloc(&p->loop_state, sizeof(LoopState), nullptr);
+        if (st != ASYRK_OK) return st;
+        ASYRK_CK(cudaStreamSynchronize(nullptr));  // in place before the loop's streams use it
         p->dev_bytes += (int64_t)sizeof(LoopState);
     }
     if (!p->cap_stream) ASYRK_CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));

@@ -203,3 +203,27 @@ def test_half_a_billion_rows_64bit_offsets():
         assert st == asyrk.OK, info.as_dict()
     del val
     torch.cuda.empty_cache()
+
+
+def test_reused_pool_memory_gives_the_same_solve_and_trim():
+    # a problem created in memory that another problem used and freed (the
+    # pool keeps it) solves bit for bit like the first problem did; trimming
+    # the pool between problems changes nothing either
+    s = synth.make_system(4096, 1024, 16, 31, row_norms="lognormal", value_dtype="f32")
+    other = synth.make_system(8192, 2048, 24, 32, row_norms="lognormal", value_dtype="f32")
+    xs = []
+    for k in range(3):
+        with asyrk.Problem.from_system(s) as p:
+            x = np.zeros(s.n)
+            st, info = p.solve(x, tol=1e-5, max_sweeps=400, x_true=s.x_true,
+                               mode=asyrk.MODE_SEQUENTIAL)
+            assert st == asyrk.OK, (st, info.as_dict())
+            xs.append(x)
+        with asyrk.Problem.from_system(other) as q:
+            y = np.full(other.n, 7.0)
+            st, _ = q.solve(y, tol=1e-3, max_sweeps=50, x_true=other.x_true)
+            assert st == asyrk.OK
+        if k == 1:
+            assert asyrk.asyrk_trim_memory() == asyrk.OK
+    np.testing.assert_array_equal(xs[0], xs[1])
+    np.testing.assert_array_equal(xs[0], xs[2])
