@@ -703,8 +703,11 @@ def extras_batched(asyrk, synth, torch, graph=True):
            "sum_nnz": int(sum(m * L for m, _, L in shapes)), "status": st,
            "converged": bi.converged, "iterations": bi.iterations, "graph_launch": bool(bi.graph),
            "engine": {1: "global iterate (L2 atomics)",
-                      2: "on-chip: one thread-block cluster per system, x in distributed shared "
-                         "memory"}.get(bi.engine, bi.engine),
+                      2: "on-chip: one CTA per system, x in its shared memory",
+                      3: "both at once on split SMs: on-chip CTAs for the members that fit, "
+                         "the global iterate for the rest"}.get(bi.engine, bi.engine),
+           "onchip_members": bi.onchip_members,
+           "global_part_ms": bi.global_ms, "onchip_part_ms": bi.onchip_ms,
            "workers_per_system_median": float(np.median([i.workers for i in infos])),
            "device_ms": bi.device_ms, "wall_ms": 1e3 * bi.seconds,
            "projections_per_s": bi.projections / (bi.device_ms / 1e3),
@@ -1066,7 +1069,7 @@ def run_asyrk(args, dist):
            "ms_per_step_split": {k: 1e3 * v / max(1, args.e2e_steps) for k, v in split.items()},
            "create_ms_each_step": create_ms,
            "host_affinity": affinity, "h2d_probe_gbs": h2d_gbs,
-           "note": "create copies 1.1 GB over the host link (~210 GB/s: ~5.2 ms of its ~7.4 ms); "
+           "note": "create copies 1.1 GB over the host link (~210 GB/s: ~5.2 ms of its ~6.3 ms); "
                    "on some boxes the link stalls for 10-60 ms about every 0.5 s whatever the "
                    "process runs, which slows the creates that meet a stall to 16-240 ms"}
 

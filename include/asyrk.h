@@ -202,7 +202,10 @@ typedef struct asyrk_problem_stats {
  *   values : nnz entries of type vdtype (BF16 as uint16 bit patterns), finite,
  *            every row with ||a_i|| > 0;
  *   b      : m doubles, finite.
- * Host arrays are read before the call returns; device arrays too.
+ * nnz = row_ptr[m]: col_idx and values must hold that many entries.  Host
+ * arrays are read before the call returns (the entries in chunks on a stream
+ * of the library's own, overlapping the checks and the row set-up); device
+ * arrays too.
  * Errors: EINVAL (m, n outside [1, 2^31-1], a malformed CSR, a zero row,
  * non-finite data, ||A||_F^2 or ||b||^2 beyond the FP64 range, bad opts),
  * ENOMEM, ECUDA.  On error *out is NULL. */
@@ -343,6 +346,9 @@ typedef struct asyrk_batch_info {
     int32_t onchip_members;   /* members the on-chip engine solved                 */
     int32_t global_sms;       /* SMs of the global engine when the SMs were split
                                  between the engines, else 0                        */
+    float global_ms;          /* CUDA-event time from the start of the loop to the
+                                 end of the global engine's part (0: no members)   */
+    float onchip_ms;          /* same, to the end of the on-chip engine's part     */
     int32_t reserved;
 } asyrk_batch_info;
 

@@ -198,6 +198,7 @@ class BatchInfo(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("resident_warps", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("onchip_members", ctypes.c_int32), ("global_sms", ctypes.c_int32),
+                ("global_ms", ctypes.c_float), ("onchip_ms", ctypes.c_float),
                 ("reserved", ctypes.c_int32)]
 
     def as_dict(self):

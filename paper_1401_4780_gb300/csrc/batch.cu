@@ -73,6 +73,7 @@ struct asyrk_batch {
     int resident_warps_glob = 0;         // the global engine's warps on its SMs
     int *onchip_list = nullptr;          // device: on-chip members grouped per launch
     cudaEvent_t ev_on_join = nullptr;
+    cudaEvent_t ev_done[2] = {nullptr, nullptr};  // end of the global / on-chip part (timed)
 };
 
 using namespace asyrk;
@@ -88,6 +89,8 @@ static void batch_free(asyrk_batch *b)
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->ev_on_join) cudaEventDestroy(b->ev_on_join);
+    for (cudaEvent_t e : b->ev_done)
+        if (e) cudaEventDestroy(e);
     sm_partition_destroy(&b->split);
     cudaFree(b->onchip_list);
     cudaFree(b->d);
@@ -409,6 +412,8 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_done[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_done[1]);
     if (e != cudaSuccess) return fail(cuda_fail(e, "batch allocation", __FILE__, __LINE__));
     for (int k = 0; k < count; ++k) {
         b->h[k].x = b->x + b->xoff[k];
@@ -595,6 +600,7 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
                 if (b->h_ints[0] == 0) break;
             }
         }
+        ASYRK_CK(cudaEventRecord(b->ev_done[0], gs));
         if (gs != s) ASYRK_CK(cudaEventRecord(b->ev_join, gs));
     }
     if (b->n_on > 0) {
@@ -610,6 +616,7 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
                     return st;
         }
         launches += b->n_on;
+        ASYRK_CK(cudaEventRecord(b->ev_done[1], os));
         if (os != s) {
             ASYRK_CK(cudaEventRecord(b->ev_on_join, os));
             ASYRK_CK(cudaStreamWaitEvent(s, b->ev_on_join, 0));
@@ -645,8 +652,15 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
         D.skipped = J.skipped;
         if (J.sweeps > iters) iters = J.sweeps;
     }
-    float ms = 0.f;
+    float ms = 0.f, part_ms[2] = {0.f, 0.f};
     ASYRK_CK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+    for (int q = 0; q < 2; ++q) {
+        if ((q == 0 ? b->n_glob : b->n_on) == 0) continue;
+        if (cudaEventElapsedTime(&part_ms[q], b->ev[0], b->ev_done[q]) != cudaSuccess) {
+            part_ms[q] = -1.f;  // a timing the driver does not give is reported as -1
+            (void)cudaGetLastError();
+        }
+    }
     const double secs =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     int worst = ASYRK_OK, converged = 0;
@@ -687,6 +701,9 @@ extern "C" int asyrk_batch_solve(asyrk_batch *b, double *const *xs, const double
         binfo->engine = (b->n_glob > 0 ? ASYRK_ENGINE_GLOBAL : 0) | (b->n_on > 0 ? ASYRK_ENGINE_ONCHIP : 0);
         binfo->onchip_members = b->n_on;
         binfo->global_sms = b->split.sms[0];
+        binfo->global_ms = part_ms[0];
+        binfo->onchip_ms = part_ms[1];
+        binfo->reserved = 0;
     }
     return worst;
 }

@@ -17,6 +17,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 
@@ -81,15 +82,15 @@ __device__ __forceinline__ bool finite_val(VT v)
 // One thread per row.  src_* index the caller's CSR layout, dst_* the padded
 // one; when no padding is needed src and dst are the same arrays.
 template <typename VT>
-__global__ void k_row_setup(int64_t m, int64_t n, const int64_t *__restrict__ row_ptr,
+__global__ void k_row_setup(int64_t r0, int64_t r1, int64_t n, const int64_t *__restrict__ row_ptr,
                             const int64_t *__restrict__ pstart, const int32_t *src_col,
                             const VT *src_val, int32_t *dst_col, VT *dst_val,
                             const double *__restrict__ b, RowRec *__restrict__ rec,
                             double *__restrict__ w64, double *__restrict__ b64,
                             unsigned *__restrict__ err)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+    const int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // rows [r0, r1)
+    if (i >= r1) return;
     const int64_t s = row_ptr[i], e = row_ptr[i + 1];
     const int64_t d = pstart ? pstart[i] : s;
     unsigned bad = 0;
@@ -143,15 +144,42 @@ static size_t value_size(int dtype)
 }
 
 template <typename VT>
-static void launch_row_setup(asyrk_problem *p, const int64_t *row_ptr_d, const int64_t *pstart_d,
-                             const int32_t *src_col, const void *src_val, const double *b_d,
-                             unsigned *err_d, cudaStream_t s)
+static void launch_row_setup(asyrk_problem *p, int64_t r0, int64_t r1, const int64_t *row_ptr_d,
+                             const int64_t *pstart_d, const int32_t *src_col, const void *src_val,
+                             const double *b_d, unsigned *err_d, cudaStream_t s)
 {
     const int T = 256;
-    const int64_t blocks = (p->m + T - 1) / T;
+    const int64_t blocks = (r1 - r0 + T - 1) / T;
     k_row_setup<VT><<<(unsigned)blocks, T, 0, s>>>(
-        p->m, p->n, row_ptr_d, pstart_d, src_col, (const VT *)src_val, p->col, (VT *)p->val, b_d,
+        r0, r1, p->n, row_ptr_d, pstart_d, src_col, (const VT *)src_val, p->col, (VT *)p->val, b_d,
         p->rec, p->w64, p->b64, err_d);
+}
+
+static void row_setup(asyrk_problem *p, int64_t r0, int64_t r1, const int64_t *row_ptr_d,
+                      const int64_t *pstart_d, const int32_t *src_col, const void *src_val,
+                      const double *b_d, unsigned *err_d, cudaStream_t s)
+{
+    if (r1 <= r0) return;
+    switch (p->dtype) {
+    case ASYRK_F64: launch_row_setup<double>(p, r0, r1, row_ptr_d, pstart_d, src_col, src_val, b_d, err_d, s); break;
+    case ASYRK_F32: launch_row_setup<float>(p, r0, r1, row_ptr_d, pstart_d, src_col, src_val, b_d, err_d, s); break;
+    default: launch_row_setup<bf16_t>(p, r0, r1, row_ptr_d, pstart_d, src_col, src_val, b_d, err_d, s); break;
+    }
+}
+
+// Host entries go to the device in chunks of about CREATE_CHUNK_BYTES on a
+// stream of their own, while the row pointers are checked and the rows of each
+// chunk that has arrived are set up.
+constexpr int64_t CREATE_CHUNK_BYTES = 64LL << 20;
+constexpr int CREATE_MAX_CHUNKS = 32;
+// entries a problem may have: every byte count below stays inside int64
+constexpr int64_t CREATE_MAX_NNZ = 1LL << 58;
+
+// first entry of chunk c of `chunks` over nnz entries
+static int64_t chunk_begin(int64_t nnz, int chunks, int c)
+{
+    const int64_t q = nnz / chunks, r = nnz % chunks;
+    return q * c + (c < r ? c : r);
 }
 
 int ensure_workspace(asyrk_problem *p)
@@ -263,12 +291,21 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
     double *b_d = nullptr;
     unsigned *err_d = nullptr;
     bool own_src = false;
+    cudaStream_t cs = nullptr;  // the host entries' copies
+    cudaEvent_t ev_go = nullptr, ev_chunk[CREATE_MAX_CHUNKS] = {};
+    int chunks = 0;
     auto cleanup = [&]() {
-        // back to the pool in the order of the stream that used them
+        // copies still in flight end before their buffers go back to the pool,
+        // which takes them in the order of the stream that used them
+        if (cs) cudaStreamSynchronize(cs);
         if (!on_dev) { devmem_free(rp_d, s); devmem_free(b_d, s); }
         if (own_src) { devmem_free(col_src, s); devmem_free(val_src, s); }
         devmem_free(ps_d, s); devmem_free(plen_d, s); devmem_free(scan_tmp, s);
         devmem_free(info_d, s); devmem_free(err_d, s);
+        for (cudaEvent_t e : ev_chunk)
+            if (e) cudaEventDestroy(e);
+        if (ev_go) cudaEventDestroy(ev_go);
+        if (cs) cudaStreamDestroy(cs);
     };
     auto fail = [&](int code) { cleanup(); return code; };
 #define ASYRK_ALLOC(ptr, bytes)                                                            \
@@ -282,13 +319,52 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
         if (e__ != cudaSuccess) return fail(cuda_fail(e__, #call, __FILE__, __LINE__));    \
     } while (0)
 
-    // 1. row pointers on the device: checks, padded row starts (a prefix sum)
+    // 1. row pointers on the device (checked below)
     if (on_dev) {
         rp_d = const_cast<int64_t *>(row_ptr);
     } else {
         ASYRK_ALLOC(rp_d, (m + 1) * sizeof(int64_t));
         ASYRK_CKC(cudaMemcpyAsync(rp_d, row_ptr, (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     }
+
+    // 2. host entries and b on their way while the row pointers are checked.
+    //    The arrays hold row_ptr[m] entries (the caller's contract; the device
+    //    copy's row_ptr[m] is compared below); chunk c is a contiguous range of
+    //    entries, copied on cs after the row pointers.
+    const size_t es = value_size(p->dtype);
+    int64_t nnz_h = 0;
+    if (!on_dev) {
+        if (row_ptr[0] != 0) return fail(set_error(ASYRK_EINVAL, "row_ptr[0] must be 0"));
+        nnz_h = row_ptr[m];
+        if (nnz_h < m || nnz_h > m * n || nnz_h > CREATE_MAX_NNZ)
+            return fail(set_error(ASYRK_EINVAL, "row_ptr[m] = %lld: every row needs an entry and "
+                                  "at most n", (long long)nnz_h));
+        own_src = true;
+        ASYRK_ALLOC(col_src, (size_t)nnz_h * 4);
+        ASYRK_ALLOC(val_src, (size_t)nnz_h * es);
+        ASYRK_ALLOC(b_d, m * sizeof(double));
+        ASYRK_CKC(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        ASYRK_CKC(cudaEventCreateWithFlags(&ev_go, cudaEventDisableTiming));
+        ASYRK_CKC(cudaEventRecord(ev_go, s));  // the allocations, the row pointers' copy
+        ASYRK_CKC(cudaStreamWaitEvent(cs, ev_go, 0));
+        ASYRK_CKC(cudaMemcpyAsync(b_d, b, m * sizeof(double), cudaMemcpyHostToDevice, cs));
+        const int64_t bytes = nnz_h * (int64_t)(4 + es);
+        chunks = (int)std::min<int64_t>(CREATE_MAX_CHUNKS,
+                                        std::max<int64_t>(1, (bytes + CREATE_CHUNK_BYTES - 1) /
+                                                                 CREATE_CHUNK_BYTES));
+        for (int c = 0; c < chunks; ++c) {
+            const int64_t z0 = chunk_begin(nnz_h, chunks, c), z1 = chunk_begin(nnz_h, chunks, c + 1);
+            ASYRK_CKC(cudaMemcpyAsync(col_src + z0, col_idx + z0, (size_t)(z1 - z0) * 4,
+                                      cudaMemcpyHostToDevice, cs));
+            ASYRK_CKC(cudaMemcpyAsync((char *)val_src + (size_t)z0 * es,
+                                      (const char *)values + (size_t)z0 * es, (size_t)(z1 - z0) * es,
+                                      cudaMemcpyHostToDevice, cs));
+            ASYRK_CKC(cudaEventCreateWithFlags(&ev_chunk[c], cudaEventDisableTiming));
+            ASYRK_CKC(cudaEventRecord(ev_chunk[c], cs));
+        }
+    }
+
+    // 3. row-pointer checks, padded row starts (a prefix sum)
     ASYRK_ALLOC(plen_d, m * sizeof(int64_t));
     ASYRK_ALLOC(ps_d, (m + 1) * sizeof(int64_t));
     ASYRK_ALLOC(scan_tmp, scan_tmp_count(m) * sizeof(int64_t));
@@ -310,50 +386,59 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
         return fail(set_error(ASYRK_EINVAL, "row %llu is empty or row_ptr decreases (the problem "
                               "has no zero rows)", info[2]));
     if (info[0] & RP_LONG) return fail(set_error(ASYRK_EINVAL, "a row has more entries than n"));
+    if (!on_dev && tail[0] != nnz_h)
+        return fail(set_error(ASYRK_EINVAL, "row_ptr changed while the problem was created"));
+    if (tail[1] > CREATE_MAX_NNZ) return fail(set_error(ASYRK_ENOMEM, "too many entries"));
     const bool aligned = !(info[0] & RP_MISALIGNED) && tail[1] == tail[0];
     p->nnz = tail[0];
     p->nnz_pad = aligned ? p->nnz : tail[1];
     p->max_len = (int64_t)info[1];
 
-    // 2. device arrays
-    const size_t es = value_size(p->dtype);
+    // 4. device arrays; staged host entries whose rows are already 4-aligned
+    //    are the handle's arrays as they stand
+    if (aligned && own_src) {
+        p->col = col_src;
+        p->val = val_src;
+        own_src = false;
+    } else {
+        if ((st = dev_alloc(p, &p->col, (size_t)p->nnz_pad, s)) != ASYRK_OK) return fail(st);
+        if ((st = dev_alloc(p, (char **)&p->val, (size_t)p->nnz_pad * es, s)) != ASYRK_OK) return fail(st);
+    }
     if ((st = dev_alloc(p, &p->rec, (size_t)m, s)) != ASYRK_OK) return fail(st);
-    if ((st = dev_alloc(p, &p->col, (size_t)p->nnz_pad, s)) != ASYRK_OK) return fail(st);
-    if ((st = dev_alloc(p, (char **)&p->val, (size_t)p->nnz_pad * es, s)) != ASYRK_OK) return fail(st);
     if ((st = dev_alloc(p, &p->b64, (size_t)m, s)) != ASYRK_OK) return fail(st);
     if ((st = dev_alloc(p, &p->w64, (size_t)m, s)) != ASYRK_OK) return fail(st);
     ASYRK_ALLOC(err_d, sizeof(unsigned));
     ASYRK_CKC(cudaMemsetAsync(err_d, 0, sizeof(unsigned), s));
 
-    // 3. the caller's entries: straight into place when rows are already
-    //    4-aligned, else through the row pass's padding copy
-    if (aligned) {
-        const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        ASYRK_CKC(cudaMemcpyAsync(p->col, col_idx, p->nnz * 4, kind, s));
-        ASYRK_CKC(cudaMemcpyAsync(p->val, values, p->nnz * es, kind, s));
-    } else if (on_dev) {
-        col_src = const_cast<int32_t *>(col_idx);
-        val_src = const_cast<void *>(values);
-    } else {
-        own_src = true;
-        ASYRK_ALLOC(col_src, p->nnz * 4);
-        ASYRK_ALLOC(val_src, p->nnz * es);
-        ASYRK_CKC(cudaMemcpyAsync(col_src, col_idx, p->nnz * 4, cudaMemcpyHostToDevice, s));
-        ASYRK_CKC(cudaMemcpyAsync(val_src, values, p->nnz * es, cudaMemcpyHostToDevice, s));
-    }
-    if (on_dev) {
-        b_d = const_cast<double *>(b);
-    } else {
-        ASYRK_ALLOC(b_d, m * sizeof(double));
-        ASYRK_CKC(cudaMemcpyAsync(b_d, b, m * sizeof(double), cudaMemcpyHostToDevice, s));
-    }
-    const int32_t *rs_col = aligned ? p->col : col_src;
-    const void *rs_val = aligned ? p->val : val_src;
+    // 5. the row pass: checks, row weights and records, and the padding copy
+    //    when rows are not 4-aligned; on host entries, the rows of each chunk
+    //    once it has arrived (rows that reach into chunk c wait for it)
     const int64_t *pstart = aligned ? nullptr : ps_d;
-    switch (p->dtype) {
-    case ASYRK_F64: launch_row_setup<double>(p, rp_d, pstart, rs_col, rs_val, b_d, err_d, s); break;
-    case ASYRK_F32: launch_row_setup<float>(p, rp_d, pstart, rs_col, rs_val, b_d, err_d, s); break;
-    default: launch_row_setup<bf16_t>(p, rp_d, pstart, rs_col, rs_val, b_d, err_d, s); break;
+    if (on_dev) {
+        const int32_t *rs_col = col_idx;
+        const void *rs_val = values;
+        if (aligned) {
+            ASYRK_CKC(cudaMemcpyAsync(p->col, col_idx, p->nnz * 4, cudaMemcpyDeviceToDevice, s));
+            ASYRK_CKC(cudaMemcpyAsync(p->val, values, p->nnz * es, cudaMemcpyDeviceToDevice, s));
+            rs_col = p->col;
+            rs_val = p->val;
+        }
+        row_setup(p, 0, m, rp_d, pstart, rs_col, rs_val, b, err_d, s);
+    } else {
+        const int32_t *rs_col = aligned ? p->col : col_src;
+        const void *rs_val = aligned ? p->val : val_src;
+        int64_t r0 = 0;
+        for (int c = 0; c < chunks; ++c) {
+            // rows whose entries lie in chunks 0..c: row_ptr[i+1] <= the chunk's end
+            const int64_t z1 = chunk_begin(p->nnz, chunks, c + 1);
+            const int64_t r1 = c == chunks - 1
+                                   ? m
+                                   : (int64_t)(std::upper_bound(row_ptr + 1, row_ptr + m + 1, z1) -
+                                               (row_ptr + 1));
+            ASYRK_CKC(cudaStreamWaitEvent(s, ev_chunk[c], 0));
+            row_setup(p, r0, r1, rp_d, pstart, rs_col, rs_val, b_d, err_d, s);
+            r0 = r1;
+        }
     }
     ASYRK_CKC(cudaGetLastError());
     unsigned err_h = 0;
@@ -368,7 +453,7 @@ static int create_impl(asyrk_problem *p, const int64_t *row_ptr, const int32_t *
         return fail(set_error(ASYRK_EINVAL, "malformed problem: %s", why));
     }
 
-    // 4. ||A||_F^2, ||b|| and the alias table of the row weights, on the GPU
+    // 6. ||A||_F^2, ||b|| and the alias table of the row weights, on the GPU
     if ((st = row_totals_and_alias(p, s)) != ASYRK_OK) return fail(st);
     cleanup();
 #undef ASYRK_CKC

@@ -227,3 +227,35 @@ def test_reused_pool_memory_gives_the_same_solve_and_trim():
             assert asyrk.asyrk_trim_memory() == asyrk.OK
     np.testing.assert_array_equal(xs[0], xs[1])
     np.testing.assert_array_equal(xs[0], xs[2])
+
+
+@pytest.mark.parametrize("lengths", [(30, 42), 36])
+def test_host_entries_in_chunks_match_a_device_created_problem(lengths):
+    # 151 MB of entries reach the device in three chunks, each chunk's rows set
+    # up as it arrives (rows of 30..42 entries: 4-misaligned starts, the padding
+    # copy; 36 per row: the staged entries kept as they are).  The same system
+    # created from device arrays (one pass) gives the same records, sums, alias
+    # table and sequential iterate, and F is the oracle's
+    import torch
+    m, n = 1 << 19, 1 << 17
+    s = synth.make_system(m, n, lengths, 77, row_norms="lognormal", value_dtype="f32")
+    assert s.row_ptr[-1] * 8 > 2 * (64 << 20)
+    seed = synth.solver_seed(s.seed)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+           for a in (s.row_ptr, s.col, s.val_store, s.b)]
+    with asyrk.Problem.from_system(s) as ph, \
+            asyrk.Problem(m, n, *dev[:3], asyrk.F32, dev[3], seed=seed, device_ptrs=True) as pd:
+        sh, sd = ph.stats(), pd.stats()
+        for k in ("nnz", "nnz_padded", "max_row_len", "frob2", "uniform"):
+            assert sh[k] == sd[k], k
+        assert (sh["nnz_padded"] == sh["nnz"]) == (lengths == 36)
+        assert sh["frob2"] == oracle.Sampler(m, s.row_ptr, s.val64).F
+        np.testing.assert_array_equal(ph.draw_rows(12345, 200000), pd.draw_rows(12345, 200000))
+        xs = []
+        for p in (ph, pd):
+            x = np.zeros(n)
+            st, info = p.solve(x, tol=0.0, max_sweeps=1, mode=asyrk.MODE_SEQUENTIAL)
+            assert st == asyrk.OK
+            xs.append(x)
+        np.testing.assert_array_equal(xs[0], xs[1])
+        assert np.isfinite(xs[0]).all() and np.linalg.norm(xs[0]) > 0

@@ -214,6 +214,10 @@ def test_hybrid_batch_reaches_tolerance(graph, partition):
             assert bi.engine == asyrk.ENGINE_ONCHIP | asyrk.ENGINE_GLOBAL
             assert 1 <= bi.onchip_members <= 5 and bi.converged == len(systems)
             assert bi.iterations == max(i.sweeps for i in infos)
+            # each engine's part ends within the timed loop
+            assert 0 < bi.global_ms <= bi.device_ms * (1 + 1e-6)
+            assert 0 < bi.onchip_ms <= bi.device_ms * (1 + 1e-6)
+            assert max(bi.global_ms, bi.onchip_ms) >= 0.5 * bi.device_ms
             if graph and partition:
                 import torch
                 sms = torch.cuda.get_device_properties(0).multi_processor_count
