@@ -82,6 +82,8 @@ def parse_args():
                     help="a second, lower offered rate (0: skip)")
     ap.add_argument("--batched-only", action="store_true",
                     help="profiling aid: run only the 256-system batched case, print its JSON")
+    ap.add_argument("--batched-systems", type=int, default=0,
+                    help="with --batched-only: the first N systems only (a reduced case for ncu)")
     ap.add_argument("--served-only", action="store_true",
                     help="tuning aid: run only the served measurement(s), print their JSON")
     ap.add_argument("--batch-host-loop", action="store_true",
@@ -639,8 +641,10 @@ def extras_lsq(asyrk, synth, torch):
             "normal_eq_rel_residual": opt}
 
 
-def extras_batched(asyrk, synth, torch, graph=True):
+def extras_batched(asyrk, synth, torch, graph=True, systems=0):
     shapes = synth.batch_shapes()
+    if systems > 0:  # profiling aid: the first `systems` members only
+        shapes = shapes[:systems]
     base = synth.config_seed(4) * 1000
     probs, x_trues = [], []
     for k, (m, n, L) in enumerate(shapes):
@@ -697,8 +701,8 @@ def extras_batched(asyrk, synth, torch, graph=True):
     # nonzero) and its 32 B record; per system, its projections x its row length
     alg_bytes = sum(i.projections * (8 * L + 32) for i, (m, n, L) in zip(infos, shapes))
     peak, peak_kind = read_peaks()
-    out = {"workload": "256 systems: m = floor(2^U(11,18)), n = m/4, nnz/row U{8..64} per system, "
-                       "N(0,1) values, unit rows, FP32; each to ||x-x*||/||x*|| <= 1e-6",
+    out = {"workload": "%d systems: m = floor(2^U(11,18)), n = m/4, nnz/row U{8..64} per system, "
+                       "N(0,1) values, unit rows, FP32; each to ||x-x*||/||x*|| <= 1e-6" % len(shapes),
            "systems": len(shapes), "sum_m": int(sum(m for m, _, _ in shapes)),
            "sum_nnz": int(sum(m * L for m, _, L in shapes)), "status": st,
            "converged": bi.converged, "iterations": bi.iterations, "graph_launch": bool(bi.graph),
@@ -1153,7 +1157,8 @@ def main():
             from paper_1401_4780_gb300 import asyrk, synth
             torch.cuda.set_device(dist.local_rank)
             asyrk.load()
-            print(json.dumps(extras_batched(asyrk, synth, torch, graph=not args.batch_host_loop)),
+            print(json.dumps(extras_batched(asyrk, synth, torch, graph=not args.batch_host_loop,
+                                            systems=args.batched_systems)),
                   flush=True)
         else:
             run_asyrk(args, dist)
