@@ -163,6 +163,15 @@ typedef struct asyrk_solve_opts {
                                 CUDA graph (a WHILE node; the host waits once per
                                 solve); 0 (default): the host drives the loop, one
                                 wait per check                                      */
+    int32_t kernel_form;     /* ASYNC/REFINE full-row projections: 0 (default) picks
+                                the latency form -- each worker loads its next
+                                projections' records and rows ahead -- for launches
+                                of at most 8 warps per SM (small systems, whose
+                                worker count Corollary 2 caps) and the throughput
+                                form above; 1 always the latency form, -1 always
+                                the throughput form.  Same projections, order per
+                                worker and delay either way.  EINVAL: another
+                                value, or 1 with UPDATE_SINGLE                       */
 } asyrk_solve_opts;
 
 typedef struct asyrk_solve_info {

@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_CONVERGED, DIVERGED = 0, -1, -2, -3, -4
 ECANCELED = -5
 MODE_SEQUENTIAL, MODE_ASYNC, MODE_REFINE = 0, 1, 2
 MEASURE_AUTO, MEASURE_RESIDUAL, MEASURE_NORMAL_RESIDUAL = 0, 1, 2
+FORM_AUTO, FORM_LATENCY, FORM_THROUGHPUT = 0, 1, -1
 SAMPLE_WEIGHTED, SAMPLE_SHUFFLED = 0, 1
 UPDATE_ROW, UPDATE_SINGLE = 0, 1
 ENGINE_AUTO, ENGINE_GLOBAL, ENGINE_ONCHIP = 0, 1, 2
@@ -53,7 +54,7 @@ class SolveOpts(ctypes.Structure):
                 ("inner_sweeps", ctypes.c_int64), ("profile", ctypes.c_int32),
                 ("row_exclusion", ctypes.c_int32), ("measure", ctypes.c_int32),
                 ("sampling", ctypes.c_int32), ("update", ctypes.c_int32),
-                ("graph_loop", ctypes.c_int32)]
+                ("graph_loop", ctypes.c_int32), ("kernel_form", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -465,12 +466,14 @@ def asyrk_problem_get_stats(h):
 # ---------------------------------------------------------------------------
 def solve_opts(mode=MODE_ASYNC, workers=0, subwarp=0, check_every=1, x_true=None, stream=None,
                inner_tol=0.0, inner_sweeps=0, profile=False, device_ptrs=False, row_exclusion=0,
-               measure=MEASURE_AUTO, sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW, graph_loop=False):
+               measure=MEASURE_AUTO, sampling=SAMPLE_WEIGHTED, update=UPDATE_ROW, graph_loop=False,
+               kernel_form=0):
     return SolveOpts(mode=mode, device_ptrs=1 if device_ptrs else 0, workers=workers,
                      subwarp=subwarp, check_every=check_every, x_true=_ptr(x_true),
                      stream=_stream(stream), inner_tol=inner_tol, inner_sweeps=inner_sweeps,
                      profile=1 if profile else 0, row_exclusion=row_exclusion, measure=measure,
-                     sampling=sampling, update=update, graph_loop=1 if graph_loop else 0)
+                     sampling=sampling, update=update, graph_loop=1 if graph_loop else 0,
+                     kernel_form=kernel_form)
 
 
 class Problem:

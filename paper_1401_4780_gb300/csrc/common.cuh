@@ -170,6 +170,7 @@ struct ProjectLaunch {
     int update = 0;                 // 0: the whole row, 1: one coordinate (Algorithm 1)
     bool b_from_rec = true;         // FP32 b from rec (else b64)
     const unsigned long long *dyn = nullptr;  // device {j0, count} (graph-captured loop)
+    int form = 0;                   // 0: by warps per SM, 1: latency form, -1: throughput form
     cudaStream_t stream = nullptr;
 };
 int launch_project(const ProjectLaunch &L);  // counts into L.p->launches

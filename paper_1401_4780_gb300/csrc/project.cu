@@ -40,7 +40,10 @@ __global__ void k_draw_rows(const RowRec *__restrict__ rec, uint2 key, unsigned 
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
-using KernelFn = void (*)(const ProjArgs);
+using KernelFn = ProjKernelFn;
+
+// launches with at most this many warps per SM run the latency form (project_pf.cu)
+constexpr long long LATENCY_FORM_WARPS_PER_SM = 8;
 
 template <typename VT, typename XT, bool SEQ, bool EXCL>
 static KernelFn pick_g(int G)
@@ -101,7 +104,12 @@ int launch_project(const ProjectLaunch &L)
     asyrk_problem *p = L.p;
     if (L.count == 0) return ASYRK_OK;
     const bool excl = L.exclusive && !L.sequential;
-    KernelFn k = pick_kernel(p->dtype, L.x_f64, L.sequential, excl, L.subwarp);
+    KernelFn k = nullptr;
+    const bool few_warps =
+        ((long long)L.workers * L.subwarp + 31) / 32 <= LATENCY_FORM_WARPS_PER_SM * p->sm_count;
+    if (!L.sequential && L.update == 0 && (L.form > 0 || (L.form == 0 && few_warps)))
+        k = pick_project_pf(p->dtype, L.x_f64, excl, L.subwarp);
+    if (!k) k = pick_kernel(p->dtype, L.x_f64, L.sequential, excl, L.subwarp);
     if (!k) return set_error(ASYRK_EINVAL, "no projection kernel for subwarp %d", L.subwarp);
     ProjArgs a;
     a.rec = p->rec;

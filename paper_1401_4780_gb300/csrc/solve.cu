@@ -320,6 +320,7 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
         L.exclusive = o.row_exclusion >= 0;
         L.sampling = o.sampling;
         L.update = o.update;
+        L.form = o.kernel_form;
         L.b_from_rec = !x_f64;
         LoopState init;
         memset(&init, 0, sizeof init);
@@ -360,6 +361,7 @@ static int solve_plain(SolveCtx &c, double gamma, double tol, int64_t max_sweeps
         L.exclusive = o.row_exclusion >= 0;
         L.sampling = o.sampling;
         L.update = o.update;
+        L.form = o.kernel_form;
         L.b_from_rec = !x_f64;
         L.stream = c.s;
         if ((st = project(c, L)) != ASYRK_OK) return st;
@@ -462,6 +464,7 @@ static int solve_refine(SolveCtx &c, double gamma, double tol, int64_t max_sweep
         L.exclusive = o.row_exclusion >= 0;
         L.sampling = o.sampling;
         L.update = o.update;
+        L.form = o.kernel_form;
         L.b_from_rec = true;
         L.stream = c.s;
         if ((st = project(c, L)) != ASYRK_OK) return st;
@@ -515,6 +518,10 @@ extern "C" int asyrk_solve(asyrk_problem *p, double *x, double gamma, double tol
     if (o.update < ASYRK_UPDATE_ROW || o.update > ASYRK_UPDATE_SINGLE)
         return set_error(ASYRK_EINVAL, "unknown update %d", o.update);
     if (o.graph_loop < 0 || o.graph_loop > 1) return set_error(ASYRK_EINVAL, "graph_loop must be 0 or 1");
+    if (o.kernel_form < -1 || o.kernel_form > 1)
+        return set_error(ASYRK_EINVAL, "kernel_form must be -1, 0 or 1");
+    if (o.kernel_form == 1 && o.update == ASYRK_UPDATE_SINGLE)
+        return set_error(ASYRK_EINVAL, "the latency form applies full-row updates only");
     if (o.mode == ASYRK_MODE_SEQUENTIAL && o.workers > 1)
         return set_error(ASYRK_EINVAL, "SEQUENTIAL mode has one worker");
 

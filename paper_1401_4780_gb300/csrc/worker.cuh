@@ -152,7 +152,6 @@ template <typename VT, typename XT, int G, bool SEQ, bool EXCL, bool DYN = true>
 __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, long long gbase,
                                                           long long W)
 {
-    constexpr int GPW = 32 / G;  // workers per warp
     constexpr int CH = 1;        // row chunks of 4G entries kept in registers (longer rows
                                  // re-read their tail for the scatter)
     constexpr bool F64 = std::is_same<XT, double>::value;
@@ -287,6 +286,189 @@ __device__ __forceinline__ unsigned long long run_workers(const ProjArgs &a, lon
     return skipped;
 #undef ASYRK_J0
 #undef ASYRK_COUNT
+}
+
+// ---------------------------------------------------------------------------
+// The latency form of run_workers, for launches with a few warps per SM (small
+// systems, whose worker count Corollary 2 caps near m / (2e lambda_max)).  There
+// a worker's projections follow one another with nothing to hide their round
+// trips to L2: the row record, the row, then the gathers.  Here a worker draws
+// its record two projections ahead and loads its row (and, with FP64 values,
+// b_i and ||a_i||^2) one ahead, and sends a projection's claim and gathers out
+// together with those loads, so that a projection waits about one round trip.
+// The projections, their order per worker and the number in flight (the delay
+// tau) are those of run_workers; the gathers of a projection whose claim fails
+// are dropped unused.  Full-row updates, i.i.d. or shuffled draws.
+// ---------------------------------------------------------------------------
+using ProjKernelFn = void (*)(const ProjArgs);
+// the latency form of the projection kernel (project_pf.cu); nullptr for an unknown G
+ProjKernelFn pick_project_pf(int dtype, bool x_f64, bool excl, int G);
+
+template <typename XT>
+struct Ahead {
+    long long start;
+    int len;  // 0: no projection (past the launch, or a lane without a worker)
+    unsigned i;
+    XT b, scale;
+    int4 cc;     // this lane's first 4-entry chunk of the row
+    XT vv[4];
+};
+
+// the record of projection t of the launch
+template <typename XT>
+__device__ __forceinline__ void pf_draw(const ProjArgs &a, bool worker, unsigned long long j0,
+                                        unsigned long long count, unsigned long long t, Ahead<XT> &q)
+{
+    constexpr bool F64 = std::is_same<XT, double>::value;
+    q.len = 0;
+    q.start = 0;
+    q.i = 0;
+    q.b = 0;
+    q.scale = 0;
+    if (!worker || t >= count) return;
+    RowRec r;
+    const unsigned long long j = j0 + t;
+    if (a.sampling == 1) {
+        q.i = shuffled_position(j, a.m, a.stream_id, a.key, a.shuf_h);
+        r = load_rec(a.rec + q.i);
+    } else {
+        q.i = draw_row(j, a.stream_id, a.key, a.m, a.uniform, a.rec, r);
+    }
+    q.start = r.start;
+    q.len = (int)r.len;
+    if (!F64) {
+        q.b = a.bvec ? (XT)__ldg(a.bvec + q.i) : (XT)r.b;
+        q.scale = (XT)r.inv;
+    }
+}
+
+// the loads of projection q that need its record: the lane's chunk of the row,
+// and b_i and ||a_i||^2 in FP64
+template <typename VT, typename XT>
+__device__ __forceinline__ void pf_fetch(const ProjArgs &a, const VT *val, int off, Ahead<XT> &q)
+{
+    constexpr bool F64 = std::is_same<XT, double>::value;
+    if (off < q.len) {
+        q.cc = ld_col4(a.col + q.start + off);
+        ld_val4(val + q.start + off, q.vv);
+    }
+    if (F64 && q.len > 0) {
+        q.b = (XT)__ldg(a.b64 + q.i);
+        q.scale = (XT)__ldg(a.w64 + q.i);
+    }
+}
+
+// Projection cur (record and chunk loaded ahead); meanwhile the row of nxt is
+// loaded and the record of the projection after nxt (t_after) is drawn into
+// cur's slot.
+template <typename VT, typename XT, int G, bool EXCL>
+__device__ __forceinline__ void pf_step(const ProjArgs &a, const VT *val, XT *x, XT gamma,
+                                        int lane, int sl, bool worker, unsigned long long j0,
+                                        unsigned long long count, unsigned long long t_after,
+                                        Ahead<XT> &cur, Ahead<XT> &nxt,
+                                        unsigned long long &skipped)
+{
+    constexpr bool F64 = std::is_same<XT, double>::value;
+    const int off = sl * 4;
+    bool act = cur.len > 0;
+    unsigned got = 1;
+    if (EXCL && act && sl == 0) got = claim_row(a.busy, cur.i);
+    const int k = cur.len - off;  // entries of the row in this lane's first chunk
+    XT xv[4] = {0, 0, 0, 0};
+    if (k > 0) {
+        xv[0] = ld_x(x + cur.cc.x);
+        if (k > 1) xv[1] = ld_x(x + cur.cc.y);
+        if (k > 2) xv[2] = ld_x(x + cur.cc.z);
+        if (k > 3) xv[3] = ld_x(x + cur.cc.w);
+    }
+    pf_fetch<VT, XT>(a, val, off, nxt);
+    Ahead<XT> nn;
+    pf_draw<XT>(a, worker, j0, count, t_after, nn);
+    if (EXCL) {
+        got = __shfl_sync(0xffffffffu, got, lane & ~(G - 1));
+        if (act && !got) {
+            act = false;
+            if (sl == 0) ++skipped;
+        }
+    }
+    XT acc = 0;
+    if (act && k > 0) {  // the order of dot4
+        acc = cur.vv[0] * xv[0];
+        if (k > 1) acc += cur.vv[1] * xv[1];
+        if (k > 2) acc += cur.vv[2] * xv[2];
+        if (k > 3) acc += cur.vv[3] * xv[3];
+    }
+    if (act) {
+        for (int o = (G + sl) * 4; o < cur.len; o += 4 * G) {  // rows longer than 4*G
+            XT v4[4];
+            const int4 c4 = ld_col4(a.col + cur.start + o);
+            ld_val4(val + cur.start + o, v4);
+            acc += dot4(v4, c4, cur.len - o, x);
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (act) {
+        XT s;
+        if (F64) {
+            s = -((gamma * (acc - cur.b)) / cur.scale);
+        } else {
+            s = -(gamma * (acc - cur.b) * cur.scale);
+        }
+        if (k > 0) scatter4(cur.vv, cur.cc, k, s, x);
+        for (int o = (G + sl) * 4; o < cur.len; o += 4 * G) {
+            XT v4[4];
+            const int4 c4 = ld_col4(a.col + cur.start + o);
+            ld_val4(val + cur.start + o, v4);
+            scatter4(v4, c4, cur.len - o, s, x);
+        }
+    }
+    if (EXCL) {
+        __syncwarp();  // the group's updates are issued before the bit is cleared
+        if (act && sl == 0) release_row(a.busy, cur.i);
+    }
+    cur.start = nn.start;
+    cur.len = nn.len;
+    cur.i = nn.i;
+    cur.b = nn.b;
+    cur.scale = nn.scale;
+}
+
+template <typename VT, typename XT, int G, bool EXCL, bool DYN = true>
+__device__ __forceinline__ unsigned long long run_workers_pf(const ProjArgs &a, long long gbase,
+                                                             long long W)
+{
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / G, sl = lane % G;
+    if (gbase >= W) return 0;  // whole warp idle
+    const bool worker = gbase + sub < W;
+    const VT *__restrict__ val = static_cast<const VT *>(a.val);
+    XT *x = static_cast<XT *>(a.x);
+    const XT gamma = (XT)a.gamma;
+    unsigned long long skipped = 0;
+    unsigned long long j0 = a.j0, count = a.count;
+    if (DYN && a.dyn) {
+        j0 = __ldcg(a.dyn);
+        count = __ldcg(a.dyn + 1);
+    }
+    const unsigned long long w = (unsigned long long)W;
+    // worker gbase+sub applies projections t = gbase + sub + k W; the two slots
+    // take turns as the current projection and the next, so that a row's loads
+    // stay in the registers they were issued to until it is worked on
+    unsigned long long t = (unsigned long long)(gbase + sub);
+    Ahead<XT> p0, p1;
+    pf_draw<XT>(a, worker, j0, count, t, p0);
+    pf_fetch<VT, XT>(a, val, sl * 4, p0);
+    pf_draw<XT>(a, worker, j0, count, t + w, p1);
+    // t0 = gbase + k W is warp-uniform: every lane reaches every shuffle and barrier
+    for (unsigned long long t0 = (unsigned long long)gbase; t0 < count; t0 += 2 * w, t += 2 * w) {
+        pf_step<VT, XT, G, EXCL>(a, val, x, gamma, lane, sl, worker, j0, count, t + 2 * w, p0, p1,
+                                 skipped);
+        if (t0 + w >= count) break;
+        pf_step<VT, XT, G, EXCL>(a, val, x, gamma, lane, sl, worker, j0, count, t + 3 * w, p1, p0,
+                                 skipped);
+    }
+    return skipped;
 }
 
 }  // namespace asyrk

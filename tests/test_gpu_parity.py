@@ -227,23 +227,51 @@ def test_frobenius_norm_is_the_correctly_rounded_sum(kind):
             oracle.draw_rows(5, 1, 0, 200_000, samp.thr, samp.alias, samp.uniform))
 
 
+@pytest.mark.parametrize("form", [asyrk.FORM_THROUGHPUT, asyrk.FORM_LATENCY])
 @pytest.mark.parametrize("subwarp", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_async_fp32_kernel_with_one_worker_matches_the_oracle(dtype, subwarp):
-    # the kernel the large asynchronous workload runs -- FP32 iterate, FP32 b
-    # and 1/||a_i||^2 from the row record, row exclusion on -- with a single
-    # worker applies the projections in order: after two sweeps its iterate is
-    # the oracle's sequential RK iterate (Eq. (2)) on the same row sequence, to
-    # FP32 accuracy; ragged rows of 1..70 entries exercise the chunk tails and
-    # the rows longer than a worker keeps in registers
+def test_async_fp32_kernel_with_one_worker_matches_the_oracle(dtype, subwarp, form):
+    # the kernels the asynchronous workloads run -- FP32 iterate, FP32 b and
+    # 1/||a_i||^2 from the row record, row exclusion on; the throughput form
+    # (the large workload's) and the latency form (small systems': records and
+    # rows loaded ahead) -- with a single worker apply the projections in
+    # order: after two sweeps the iterate is the oracle's sequential RK iterate
+    # (Eq. (2)) on the same row sequence, to FP32 accuracy; ragged rows of
+    # 1..70 entries exercise the chunk tails and the rows longer than a worker
+    # keeps in registers
     s = synth.make_system(3000, 800, (1, 70), 515, row_norms="lognormal", value_dtype=dtype)
     seed = synth.solver_seed(s.seed)
     with asyrk.Problem.from_system(s) as p:
         x = np.zeros(s.n)
         st, info = p.solve(x, tol=0.0, max_sweeps=2, mode=asyrk.MODE_ASYNC, workers=1,
-                           subwarp=subwarp)
+                           subwarp=subwarp, kernel_form=form)
         assert st == asyrk.OK  # tol = 0: the sweep budget ends the solve
         assert info.workers == 1 and info.subwarp == subwarp and info.skipped == 0
         assert info.projections == 2 * s.m
     xo = _oracle_steps(s, seed, 2 * s.m)
     assert _rel(x, xo) <= 2e-5
+
+
+@pytest.mark.parametrize("form", [asyrk.FORM_THROUGHPUT, asyrk.FORM_LATENCY])
+@pytest.mark.parametrize("subwarp", [1, 4, 32])
+def test_async_fp64_kernel_with_one_worker_matches_the_oracle(subwarp, form):
+    # the ASYNC FP64 kernels of both forms (FP64 iterate, b_i and ||a_i||^2 in
+    # FP64, the oracle's division) with one worker: the oracle's iterate to 1e-12
+    # after two sweeps of ragged, lognormal rows
+    s = synth.make_system(3000, 800, (1, 70), 516, row_norms="lognormal")
+    seed = synth.solver_seed(s.seed)
+    with asyrk.Problem.from_system(s) as p:
+        x = np.zeros(s.n)
+        st, info = p.solve(x, tol=0.0, max_sweeps=2, mode=asyrk.MODE_ASYNC, workers=1,
+                           subwarp=subwarp, kernel_form=form)
+        assert st == asyrk.OK and info.workers == 1 and info.projections == 2 * s.m
+    assert _rel(x, _oracle_steps(s, seed, 2 * s.m)) <= 1e-12
+
+
+def test_kernel_form_option_is_checked():
+    s = synth.make_system(64, 16, 4, 9)
+    with asyrk.Problem.from_system(s) as p:
+        x = np.zeros(s.n)
+        assert p.solve(x, kernel_form=2, raise_on_error=False)[0] == asyrk.EINVAL
+        assert p.solve(x, kernel_form=asyrk.FORM_LATENCY, update=asyrk.UPDATE_SINGLE,
+                       raise_on_error=False)[0] == asyrk.EINVAL
