@@ -433,6 +433,15 @@ def extras_plain_refine(asyrk, synth):
         st, i = _timed_solve(p, x, tol=1e-8, max_sweeps=400, x_true=s1.x_true)
         out["plain_f64_async_to_1e-8"] = {"status": st, "ms": 1e3 * i.seconds, "sweeps": i.sweeps,
                                           "rel_err": i.rel_err, "workers": i.workers}
+        # the same FP64 system through refinement: FP32 inner sweeps on the FP64
+        # values, the residual, norms and update in FP64 (this GPU's FP64 rate is low)
+        for tol in (1e-8, 1e-10):
+            st, i = _timed_solve(p, x, tol=tol, max_sweeps=2000, x_true=s1.x_true,
+                                 mode=asyrk.MODE_REFINE)
+            out["f64_values_refine_to_%g" % tol] = {"status": st, "ms": 1e3 * i.seconds,
+                                                    "sweeps": i.sweeps,
+                                                    "refine_steps": i.refine_steps,
+                                                    "rel_err": i.rel_err}
     s3 = synth.bf16_refine_system()
     s3f = synth.make_system(s3.m, s3.n, 16, s3.seed, row_norms="unit", value_dtype="f32")
     with asyrk.Problem.from_system(s3) as p:
