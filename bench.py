@@ -1099,9 +1099,12 @@ def run_asyrk(args, dist):
     extras = None
     if dist.rank == 0 and not args.no_extras:
         # each extra measurement is reported on its own: one that fails records its
-        # error instead of taking the benchmark line down with it
+        # error instead of taking the benchmark line down with it.  Each starts with
+        # the problem memory pool trimmed, so that it does not inherit the memory the
+        # previous one freed (measured: 50.5 against 49.9 ms on the batched workload)
         def guarded(fn, *a):
             try:
+                asyrk.asyrk_trim_memory()
                 return fn(*a)
             except Exception as exc:  # noqa: BLE001 -- reported, not swallowed
                 try:
