@@ -337,8 +337,11 @@ typedef struct asyrk_batch_opts {
                                estimate; 1: one worker, projections strictly in order) */
     int32_t partition;      /* both engines at once, graph form: >= 0 splits the SMs
                                between them, each engine on its own SMs, where the
-                               driver offers SM partitions (default); -1: both
-                               engines share every SM                               */
+                               driver offers SM partitions: 0 (default) sizes the
+                               on-chip engine's share from its members' estimated
+                               work, > 0 gives it that many SMs (kept within
+                               [8, SMs - 8], rounded to the driver's granularity);
+                               -1: both engines share every SM                      */
 } asyrk_batch_opts;
 
 typedef struct asyrk_batch_info {

@@ -378,7 +378,8 @@ def asyrk_batch_create(handles, stream=None, graph=True, row_exclusion=0,
     hs = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
     o = BatchOpts(stream=_stream(stream), graph=0 if graph else -1, row_exclusion=row_exclusion,
                   sampling=sampling, update=update, engine=engine, cluster_max=cluster_max,
-                  workers=workers, partition=0 if partition else -1)
+                  workers=workers,
+                  partition=(partition if not isinstance(partition, bool) else (0 if partition else -1)))
     st = load().asyrk_batch_create(ctypes.byref(b), hs, len(handles), ctypes.byref(o))
     return st, b
 

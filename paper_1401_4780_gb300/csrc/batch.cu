@@ -475,7 +475,9 @@ extern "C" int asyrk_batch_create(asyrk_batch **out, asyrk_problem *const *probl
             area += t * (double)b->shapes[k].threads;
             single = single && b->shapes[k].C == 1;
         }
-        int on_sms = (int)ceil(2.5 * area / (THREADS_PER_SM * (longest > 0.0 ? longest : 1.0)));
+        int on_sms = o.partition > 0
+                         ? o.partition
+                         : (int)ceil(2.5 * area / (THREADS_PER_SM * (longest > 0.0 ? longest : 1.0)));
         on_sms = std::max(8, std::min(on_sms, sms - 8));
         if (single && sm_partition_create(dev, sms - on_sms, &b->split)) {
             b->resident_warps_glob =

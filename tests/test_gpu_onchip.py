@@ -196,7 +196,7 @@ def test_engine_selection():
             assert bi.engine == asyrk.ENGINE_GLOBAL
 
 
-@pytest.mark.parametrize("graph,partition", [(True, True), (True, False), (False, True)])
+@pytest.mark.parametrize("graph,partition", [(True, True), (True, False), (False, True), (True, 24)])
 def test_hybrid_batch_reaches_tolerance(graph, partition):
     # two members exceed a CTA's shared memory (x alone 256 KiB): global engine.
     # Graph-launched, the two engines run at once, by default each on its own
@@ -222,6 +222,8 @@ def test_hybrid_batch_reaches_tolerance(graph, partition):
                 import torch
                 sms = torch.cuda.get_device_properties(0).multi_processor_count
                 assert 8 <= bi.global_sms <= sms - 8
+                if partition is not True:  # the on-chip engine's SMs, asked for
+                    assert abs((sms - bi.global_sms) - partition) <= 8
             else:
                 assert bi.global_sms == 0
         for s, x, info, p in zip(systems, xs, infos, probs):
