@@ -424,11 +424,10 @@ __device__ __forceinline__ void cluster_solve(ClusterJob *jobs, int k)
                 const long long start = act ? r.start : 0;
                 int len = act ? (int)r.len : 0;
                 const float b = (bvec && act) ? __ldcg(bvec + i) : r.b, scale = r.inv;
-                nact = worker && t + (unsigned long long)W < m;
-                if (nact) prefetch_draw(jbase + t + W, J, rec, m, ni, ncoin, nr);
                 // a lane's first two chunks of 4 entries (rows up to 8G entries) stay
                 // in registers from the dot product to the update (one chunk when a
-                // single lane walks the row)
+                // single lane walks the row); their loads go out before the next
+                // draw's Philox work, which then runs while they are in flight
                 int4 cc, cc1;
                 float vv[4], vv1[4];
                 const int off0 = sl * 4, off1 = G > 1 ? (G + sl) * 4 : 0x7fffffff;
@@ -441,6 +440,8 @@ __device__ __forceinline__ void cluster_solve(ClusterJob *jobs, int k)
                     cc1 = ld_col4(col + start + off1);
                     ld_val4(val + start + off1, vv1);
                 }
+                nact = worker && t + (unsigned long long)W < m;
+                if (nact) prefetch_draw(jbase + t + W, J, rec, m, ni, ncoin, nr);
                 if (excl) {
                     unsigned got = 0;
                     if (act && sl == 0) {

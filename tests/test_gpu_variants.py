@@ -101,6 +101,22 @@ def test_sequential_iterate_matches_oracle(name, sampling, update, subwarp):
     assert _rel(x, xo) <= 1e-12
 
 
+@pytest.mark.parametrize("form", [asyrk.FORM_THROUGHPUT, asyrk.FORM_LATENCY])
+def test_async_one_worker_shuffled_sweeps_match_oracle(form):
+    # both forms of the ASYNC kernel on Section 5's shuffled sweeps: with one
+    # worker the iterate is the oracle's sequential one on the same permutations
+    s = synth.make_system(3001, 700, (1, 40), 8, row_norms="lognormal", value_dtype="f64")
+    seed = synth.solver_seed(s.seed)
+    with asyrk.Problem.from_system(s) as p:
+        x = np.zeros(s.n)
+        st, info = p.solve(x, gamma=0.7, tol=0.0, max_sweeps=3, mode=asyrk.MODE_ASYNC,
+                           workers=1, subwarp=4, sampling=asyrk.SAMPLE_SHUFFLED,
+                           kernel_form=form)
+        assert st == asyrk.OK and info.projections == 3 * s.m
+    xo = _oracle_iterate(s, seed, 3 * s.m, 0.7, oracle.SAMPLE_SHUFFLED, oracle.UPDATE_ROW)
+    assert _rel(x, xo) <= 1e-12
+
+
 def test_async_shuffled_converges():
     s = synth.plain_f64_system()
     with asyrk.Problem.from_system(s) as p:
