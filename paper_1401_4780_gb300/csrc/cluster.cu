@@ -263,6 +263,8 @@ struct SolveState {
     double ref_in;       // refinement: ||r|| of the current inner solve
     double res2;         // refinement: ||b - A x64||^2 of the last outer step
     double inner_goal;   // refinement: this outer step's inner target
+    double rprev;        // refinement: ||r|| of the previous outer step (< 0: none)
+    long long inner_plan;  // refinement: inner sweeps this outer step runs
     long long sweeps, inner_sweeps;
     int status, outer_steps;
     int done, outer_next;
@@ -334,6 +336,8 @@ __device__ __forceinline__ void cluster_solve(ClusterJob *jobs, int k)
         ss.ref_in = 1.0;
         ss.res2 = 0.0;
         ss.inner_goal = J.inner_tol;
+        ss.rprev = -1.0;
+        ss.inner_plan = J.max_inner < 8 ? (J.max_inner > 0 ? J.max_inner : 1) : 8;
         ss.status = ASYRK_NOT_CONVERGED;
         ss.outer_steps = 0;
         ss.inner_sweeps = 0;
@@ -395,6 +399,24 @@ __device__ __forceinline__ void cluster_solve(ClusterJob *jobs, int k)
                 ss.ref_in = rnorm;
                 ss.inner_sweeps = 0;
                 ss.inner_goal = refine_inner_goal(J.inner_tol, J.tol, meas);
+                // the inner sweep count, as single solves plan it: from the
+                // contraction the last step's sweeps achieved, the count that
+                // meets this step's target (at least 2, at most 4x the last)
+                if (ss.rprev > 0.0 && rnorm > 0.0) {
+                    const double rho = rnorm / ss.rprev;
+                    long long inner = ss.inner_plan;
+                    if (rho > 0.0 && rho < 1.0) {
+                        double want = (double)inner * log(ss.inner_goal) / log(rho);
+                        if (want < 2.0) want = 2.0;
+                        if (want > 4.0 * (double)inner) want = 4.0 * (double)inner;
+                        inner = (long long)ceil(want);
+                    } else {
+                        inner *= 2;
+                    }
+                    if (inner > J.max_inner) inner = J.max_inner;
+                    ss.inner_plan = inner > 0 ? inner : 1;
+                }
+                ss.rprev = rnorm;
             }
             cl_sync<DS>();  // r32 complete before the inner solve reads it; decisions visible
             continue;
@@ -523,20 +545,18 @@ __device__ __forceinline__ void cluster_solve(ClusterJob *jobs, int k)
             }
         }
         cl_sync<DS>();  // the sweep's updates are all applied
-        cluster_measure<VT, DS>(J, X, xs, rank, C, J.xt != nullptr && !refine, bvec, wsum,
-                                cta_part, tot, t0, t1);
+        // inner solves run their planned sweeps unmeasured (the outer step
+        // measures); plain solves measure every sweep
+        if (!refine)
+            cluster_measure<VT, DS>(J, X, xs, rank, C, J.xt != nullptr, bvec, wsum, cta_part,
+                                    tot, t0, t1);
         if (threadIdx.x == 0) {
             ss.sweeps = sweeps + 1;
-            if (refine) {  // inner solve: ||r - A d|| / ||r||
+            if (refine) {
                 ss.inner_sweeps += 1;
-                const double mi = sqrt(t0) / ss.ref_in;
-                if (!isfinite(mi)) {
-                    ss.status = ASYRK_DIVERGED;
-                    ss.done = 1;
-                } else if (mi <= ss.inner_goal || ss.inner_sweeps >= J.max_inner ||
-                           ss.sweeps >= J.max_sweeps) {
+                if (ss.inner_sweeps >= ss.inner_plan || ss.inner_sweeps >= J.max_inner ||
+                    ss.sweeps >= J.max_sweeps)
                     ss.outer_next = 1;
-                }
             } else {
                 const double meas = sqrt(t0) / ref;
                 ss.meas = meas;
