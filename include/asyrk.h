@@ -390,22 +390,21 @@ void asyrk_batch_destroy(asyrk_batch *b);
  * resident problem (FP32 or BF16 values) and bring x0, optionally x*, gamma,
  * a tolerance and a mode: ASYNC (FP32 iterate) or REFINE (FP64 iterate, each
  * outer step r = b - A x in FP64 then an FP32 inner solve of A d = r aimed at
- * a relative residual of inner_tol: checked at every engine step in the shared
- * step; on-chip, run for the sweep count that the previous outer step's
- * contraction says meets it, as asyrk_solve plans it).  An engine thread
- * admits queued requests into free slots while the device-memory budget
- * allows -- each request's iterate, staging, claim bits and residual, plus its
- * problem's bytes counted once while any request uses it -- and advances the
- * admitted requests together in engine steps of one kernel launch, each step
- * at least 512 projections per worker long, in which a request runs as many
- * whole sweeps as fit but no more than it is predicted to still need; requests
- * whose problem fits a CTA's
- * shared memory are solved on-chip instead, one CTA each, on SMs of their own
- * (onchip, partition).  A request that finishes frees its slot for the next.
- * Each request
- * draws its own row sequence (Philox stream = its ticket), so one problem can
- * serve several requests at once.  The problems must outlive their requests;
- * the server must outlive every wait on it.
+ * a relative residual of inner_tol: checked at every engine step in the
+ * shared step; on-chip, run for the sweep count that the previous outer
+ * step's contraction says meets it, as asyrk_solve plans it).  An engine
+ * thread admits queued requests into free slots while the device-memory
+ * budget allows -- each request's iterate, staging, claim bits and residual,
+ * plus its problem's bytes counted once while any request uses it -- and
+ * advances the admitted requests together in engine steps of one kernel
+ * launch, each step at least 512 projections per worker long, in which a
+ * request runs as many whole sweeps as fit but no more than it is predicted
+ * to still need; requests whose problem fits a CTA's shared memory are solved
+ * on-chip instead, one CTA each, on SMs of their own (onchip, partition).  A
+ * request that finishes frees its slot for the next.  Each request draws its
+ * own row sequence (Philox stream = its ticket), so one problem can serve
+ * several requests at once.  The problems must outlive their requests; the
+ * server must outlive every wait on it.
  * ------------------------------------------------------------------------ */
 typedef struct asyrk_server asyrk_server; /* opaque */
 
