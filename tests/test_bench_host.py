@@ -1,5 +1,6 @@
 """Host-side logic of bench.py on the CPU: the replica aggregation over ranks
-(world size 2, gloo), the clock-record parser and the traffic-record check."""
+(world size 2, gloo), the clock-record parser, the traffic-record check and the
+reference arm's JSON line (the oracle timed on the host)."""
 import json
 import os
 import socket
@@ -88,3 +89,23 @@ def test_traffic_record_requires_matching_kernel_sources(tmp_path, monkeypatch):
     assert bench.recorded_traffic() == 1234.5
     f.write_text("source_sha256: 0000\ndram_bytes_per_launch: 1234.5\n")
     assert bench.recorded_traffic() is None
+
+
+def test_reference_arm_prints_the_contract_line():
+    # bench.py --impl reference times the FP64 oracle on the host cores on the
+    # GPU arm's workload and metric; its one JSON line carries impl, the
+    # metric's value and unit, a cpu_baseline describing the run, and an e2e
+    # record of the same value with no host-device traffic
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["unit"] == "row projections/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert d["config"]["m"] == 1 << 22 and d["config"]["nnz_per_row"] == 32
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
